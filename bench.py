@@ -1,0 +1,326 @@
+#!/usr/bin/env python3
+"""Throughput of the cross-spectrum FRB search: dedispersed fringe-search cells/s.
+
+cells = baselines x DM trials x APs x frequency points (nominal, every AP counted).
+One step = one frbx_search call: shift table, every half-overlapped segment of every
+window / baseline / DM fitted on the SBD x MBD grid, Eq. 6 + threshold, single-pulse
+extraction, DM merge, cross-matching and the all-baseline power sum.
+
+Default workload ("vgos"): 15 baselines, 4 bands x 8 subbands x 32 MHz x 64 points
+(2048 points), 0.5 ms APs, T = 20000, 512 DM trials 0..2000, windows 1..32 APs,
+synthetic seeded data (synth.make_vgos).  The cube (4.9 GB) is larger than L2.
+
+--gpus N > 1 (under torchrun): N independent replicas of the whole search, one per GPU
+(the method has no exchange step between them); value = all ranks' cells / slowest time.
+--impl reference: the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12  # 80.5
+# DRAM bytes per fitted segment of the fit kernel, from the ncu capture summarised in
+# profiles/fit_fft_vgos.md (None until a capture of the current kernel exists).
+FIT_DRAM_BYTES_PER_SEGMENT = None
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="frbx", choices=["frbx", "reference"])
+    ap.add_argument("--workload", default="vgos", choices=["vgos", "small", "vgos-slice"])
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel", type=int, default=0)
+    return ap.parse_args()
+
+
+def make_workload(name):
+    if name == "vgos":
+        wl = synth.make_vgos()
+        combos = [(1 << wl.n_bl) - 1]
+    elif name == "vgos-slice":   # small case of the same kernel, for profiler captures
+        wl = synth.make_vgos(T=2400, n_bl=1, n_dm=8)
+        wl.dms = np.linspace(0.0, 200.0, 8)
+        combos = [1]
+    else:
+        wl = synth.make_small()
+        combos = [0b111, 0b011, 0b101, 0b110]
+    return wl, combos
+
+
+def workload_config(name, wl):
+    return {"workload": f"{name}: {wl.n_bl} baselines x {len(wl.dms)} DM trials x {wl.T} APs x {wl.C} points "
+                        f"({wl.n_chan} subbands x {wl.n_point}), windows {wl.windows}",
+            "n_bl": wl.n_bl, "n_dm": int(len(wl.dms)), "T": wl.T, "n_point_total": wl.C,
+            "windows": wl.windows, "l2_flush": "inputs larger than L2 (cube %.2f GB)" % (wl.n_bl * wl.T * wl.C * 8 / 1e9)}
+
+
+def cells_of(wl):
+    return float(wl.n_bl) * len(wl.dms) * wl.T * wl.C
+
+
+def n_segments(wl, dk_max):
+    tot = 0
+    for d in range(len(wl.dms)):
+        for l in wl.windows:
+            r = wl.T - int(dk_max[d]) - l
+            if r >= 0:
+                tot += r // max(1, l // 2) + 1
+    return tot * wl.n_bl
+
+
+def fft_flops_per_segment(N, Ls, Lm):
+    """Algorithmic work of the 2-D FFT form of Sec. 5.1: N FFTs of Ls, Ls FFTs of Lm
+    (5 L log2 L each), plus |G|^2 and the compare (3 per cell)."""
+    return N * 5 * Ls * math.log2(Ls) + Ls * 5 * Lm * math.log2(Lm) + 3 * Ls * Lm
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(k)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample_rows(wl, dk_max, n_dm_s, ts):
+    """Segments of baseline 0, n_dm_s DM trials spread over the grid, APs [0, ts)."""
+    from oracle import reference as R
+    ds = np.unique(np.linspace(0, len(wl.dms) - 1, n_dm_s).round().astype(int))
+    rows = []
+    for d in ds:
+        for l in wl.windows:
+            nv = R.n_valid(wl.T, l, int(dk_max[d]))
+            step = R.window_step(l)
+            for s in range(nv):
+                if s * step >= ts:
+                    break
+                rows.append((0, int(d), l, s * step))
+    return np.array(rows, np.int32), len(ds)
+
+
+def run_oracle_sample(wl, vis0, target_s):
+    """Time the oracle's fit on a bounded sample; returns cells/s, cores, description."""
+    from oracle import reference as R
+    from oracle import _clib
+    st = R.setup_from_workload(wl)
+    dk = R.shift_table(st, wl.dms)
+    dk_max = dk.max(axis=1)
+    cube = vis0[None]
+    n_dm_s = 16
+    ts = 16
+    rows, nd = oracle_sample_rows(wl, dk_max, n_dm_s, ts)
+    t0 = time.perf_counter()
+    R.fit_segments(st, cube, dk, rows)
+    pilot = time.perf_counter() - t0
+    ts = int(max(16, min(wl.T, ts * target_s / max(pilot, 1e-3))))
+    rows, nd = oracle_sample_rows(wl, dk_max, n_dm_s, ts)
+    t0 = time.perf_counter()
+    R.fit_segments(st, cube, dk, rows)
+    dt = time.perf_counter() - t0
+    cells = 1.0 * nd * ts * wl.C
+    desc = (f"oracle FP64 fit of baseline 0, {nd} of {len(wl.dms)} DM trials, APs [0, {ts}) of {wl.T}, all "
+            f"{len(wl.windows)} windows: {rows.shape[0]} segments in {dt:.1f} s "
+            "(normalisation and extraction excluded: <1% of its time)")
+    return cells / dt, _clib.num_threads(), desc, dt
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    wl, combos = make_workload(args.workload)
+    cfg = workload_config(args.workload, wl)
+    cfg["parallelism"] = f"replicas x{world}" if world > 1 else "single GPU"
+    metric = "dedispersed fringe-search cells/s (bl x DM x bin x chan)"
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        vis0 = synth.generate_baseline(wl, 0)
+        per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+        vals = []
+        for i in range(args.warmup + args.steps):
+            v, cores, desc, dt = run_oracle_sample(wl, vis0, per_step)
+            if i >= args.warmup:
+                vals.append((v, dt))
+        v = statistics.median(x for x, _ in vals)
+        ms = statistics.mean(dt for _, dt in vals) * 1e3
+        line = {"impl": "reference", "metric": metric, "value": v, "unit": "cells/s", "n_gpus": 0,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded, synth.py)",
+                "config": cfg, "cpu_baseline": {"value": v, "unit": "cells/s", "cores": cores, "kind": "oracle",
+                                                "sample": desc},
+                "e2e": {"value": v, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1801_02391_gb300 import _build
+    _build.build()
+    from paper_1801_02391_gb300 import frbx
+
+    t_gen = time.perf_counter()
+    vis_host = synth.generate(wl)
+    t_gen = time.perf_counter() - t_gen
+    vis_pinned = torch.from_numpy(vis_host).pin_memory()
+    vis_dev = vis_pinned.to("cuda", non_blocking=False)
+    stream = torch.cuda.current_stream()
+    h = frbx.Handle.from_workload(wl)
+    dk_max = h.shift_table(wl.dms).max(axis=1)
+    n_seg = n_segments(wl, dk_max)
+    cells = cells_of(wl)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def step(vis):
+        return h.search(vis, wl.dms, wl.windows, combos=combos, kernel=args.kernel, stream=stream)
+
+    for _ in range(args.warmup):
+        out = step(vis_dev)
+    barrier()
+    clk = Clocks(local)
+    clk.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fit_ms, launches = [], 0
+    ev0.record(stream)
+    for _ in range(args.steps):
+        out = step(vis_dev)
+        fit_ms.append(h.stage_times()["fit"])
+        launches += out["launches"]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    stages = h.stage_times()
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * cells / (ms / 1e3)
+
+    # end to end through the public API from pinned host memory
+    e2e_ms = []
+    h2d = wl.n_bl * wl.T * wl.C * 8
+    d2h = 0
+    for _ in range(max(1, args.e2e_steps)):
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        o = step(vis_pinned)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+        d2h = 4 * len(wl.dms) + 16 + 28 * o["counts"]["events_baseline"] + \
+            28 * (o["counts"]["events"] - o["counts"]["events_baseline"]) + 16 * (1 + len(combos))
+    e2e = statistics.mean(e2e_ms)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e = float(t.item())
+
+    flops = n_seg * fft_flops_per_segment(wl.n_chan, h.Ls, h.Lm)
+    fit_mean = statistics.mean(fit_ms)
+    achieved = flops / (fit_mean / 1e3) / 1e12
+    roof = {"bound": "alu", "kernel": "k_fit_fft" if (h.Ls % 32 == 0 and h.Lm % 32 == 0 and args.kernel != 1)
+            else "k_fit_direct", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP32_PEAK_TFLOPS,
+            "traffic": None if FIT_DRAM_BYTES_PER_SEGMENT is None else FIT_DRAM_BYTES_PER_SEGMENT * n_seg,
+            "peak_note": "FP32 CUDA-core peak 152 SM x 128 lanes x 2 flop x 2070 MHz (derived, not measured)",
+            "work": f"{n_seg} segments x {fft_flops_per_segment(wl.n_chan, h.Ls, h.Lm):.0f} flop (2-D FFT count)",
+            "fit_ms": fit_mean, "hbm_frac_8B_per_cell": (8.0 * cells / (ms / 1e3)) / 6687.5e9}
+
+    line = {"metric": metric, "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded, synth.py)", "config": cfg,
+            "e2e": {"value": world * cells / (e2e / 1e3), "unit": "cells/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e},
+            "gpu_launches": launches, "roofline": roof, "clocks": clocks,
+            "stages_ms": stages, "segments_per_step": n_seg,
+            "pulses": int(out["counts"]["pulses"]), "groups": int(out["counts"]["groups"])}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, desc, dt = run_oracle_sample(wl, vis_host[0], args.cpu_seconds)
+        line["cpu_baseline"] = {"value": v, "unit": "cells/s", "cores": cores, "kind": "oracle", "sample": desc}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,309 @@
+/*
+ * frbx.h -- C ABI of the GB300 cross-spectrum FRB search library (libfrbx).
+ *
+ * Method: Liu, Tong, Zheng, Zhang & Tong, "A Fast Radio Burst Search Method for
+ * VLBI Observation" (arxiv 1801.02391).  Cross spectra go in; the DM grid,
+ * window set, delay search windows and baseline combinations are parameters;
+ * per-baseline single pulses, cross-match groups and combined-baseline pulses
+ * come out (the problem statement of Sec. 2).
+ *
+ * Conventions (all entry points):
+ *  - Plain C types only.  Every pointer is a host pointer unless the argument
+ *    name ends in "_dev" or a flag says otherwise; device pointers are CUDA
+ *    global-memory addresses on the handle's device.
+ *  - Return value: FRBX_OK (0) or a negative FRBX_E* code.  No C++ exception
+ *    crosses the ABI.  frbx_last_error() gives a message for the last failure
+ *    on a handle.
+ *  - A handle is not thread-safe; use one handle per host thread.  All device
+ *    work of a call is issued on the caller's stream (cudaStream_t passed as
+ *    void*, NULL = legacy default stream) and the call returns after that
+ *    stream's work for the call has finished.
+ *  - The library never frees caller memory.  It owns its own device scratch
+ *    (shift table, segment series, event lists) inside the handle and grows
+ *    it on demand; frbx_destroy() releases it.
+ */
+#ifndef FRBX_H
+#define FRBX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FRBX_OK 0
+#define FRBX_EINVAL (-1)      /* bad argument (message says which) */
+#define FRBX_ENOMEM (-2)      /* device or host allocation failed */
+#define FRBX_ECUDA (-3)       /* a CUDA runtime call failed */
+#define FRBX_ETRUNC (-4)      /* an output array was too small; *_count holds the size needed */
+#define FRBX_ETIMEOUT (-5)    /* a bounded device wait gave up */
+#define FRBX_EUNSUPPORTED (-6) /* shape outside what the kernels support (message says why) */
+
+typedef struct frbx_handle frbx_handle;
+
+/*
+ * Observing setup (Sec. 2.2, Sec. 2.3, Eq. 5).
+ *  n_chan        N sky-frequency channels (subbands), 1..64.
+ *  n_point       J frequency points per channel, 2..256.  Point j of channel n
+ *                sits at f(n,j) = f0_mhz[n] + (j * f_bw_mhz) / J  (USB).
+ *  f0_mhz        [n_chan] channel edge frequencies, MHz.  Offsets between channels
+ *                must be whole kHz; the MBD grid step df_grid is their GCD.
+ *  f_bw_mhz      channel bandwidth, MHz.
+ *  t_ap_ms       AP (accumulation period) length, ms.
+ *  f_ref_dm_mhz  reference frequency of Eq. 1; 0 = the highest point frequency.
+ *  chan_delay_ns optional [n_chan] channel delays dtau0_n (Eq. 5); NULL = 0.
+ *  chan_phase_rad optional [n_chan] initial phases dphi0_n (Eq. 5); NULL = 0.
+ *  flag          optional [n_chan*n_point], nonzero = point excluded from the fit
+ *                (j = 0 is always excluded, Sec. 2.3); NULL = none.
+ *  sbd_pad       SBD grid Ls = sbd_pad * J (zero padding of App. B); 0 = 2.
+ *  mbd_pad       MBD grid Lm = mbd_pad * nextpow2(max g_n + 1); 0 = 2.
+ *                Ls and Lm must be powers of two, Ls <= 1024, Lm <= 4096,
+ *                Ls * Lm <= 2^20.
+ * The arrays are copied; the caller may free them after frbx_create returns.
+ */
+typedef struct frbx_setup {
+  int32_t n_chan;
+  int32_t n_point;
+  const double *f0_mhz;
+  double f_bw_mhz;
+  double t_ap_ms;
+  double f_ref_dm_mhz;
+  const double *chan_delay_ns;
+  const double *chan_phase_rad;
+  const uint8_t *flag;
+  int32_t sbd_pad;
+  int32_t mbd_pad;
+} frbx_setup;
+
+/*
+ * Search parameters (Sec. 2.4).
+ *  threshold     normalised-power threshold, P > threshold (Sec. 2.4.1: 3).
+ *  nwin_min      N_win,min of step d (Sec. 3.4.1: 3).
+ *  sbd_win_ns    SBD search window [lo, hi] in ns; lo > hi means the whole grid.
+ *  mbd_win_ns    MBD search window [lo, hi] in ns; lo > hi means the whole grid.
+ *                A cell is searched when lo <= delay <= hi, with
+ *                SBD(m) = ((s(m) * J) * 1000) / (Ls * f_bw) and
+ *                MBD(q) = (s(q) * 1000) / (Lm * df_grid), s(i) = i if i < L/2 else i - L.
+ *  combos        [n_combo] baseline bit masks for the power-summation scheme
+ *                (Sec. 2.4.2); bit b = baseline b.  May be NULL when n_combo = 0.
+ *  kernel        0 = choose automatically, 1 = direct-DFT fit kernel,
+ *                2 = FFT fit kernel (needs Ls and Lm multiples of 32).
+ */
+typedef struct frbx_params {
+  float threshold;
+  int32_t nwin_min;
+  double sbd_win_ns[2];
+  double mbd_win_ns[2];
+  const uint64_t *combos;
+  int32_t n_combo;
+  int32_t kernel;
+} frbx_params;
+
+/* One fitted time segment (Sec. 5.1): max |G| over the searched grid and its cell. */
+typedef struct frbx_seg {
+  float amp;
+  uint16_t sbd_idx; /* m */
+  uint16_t mbd_idx; /* q */
+} frbx_seg;
+
+/* A threshold crossing, "candidate signal" of Sec. 2.4.1 step a. */
+typedef struct frbx_event {
+  int32_t series; /* baseline index, or combination index for combined series */
+  int32_t dm_idx;
+  int32_t win_idx; /* index into the caller's window list */
+  int32_t k0;      /* start AP of the segment (at the DM reference frequency) */
+  float amp;       /* |G| (combined series: summed amplitude) */
+  float pnorm;     /* normalised power, Eq. 6 */
+  uint16_t sbd_idx, mbd_idx; /* 0 for combined series */
+} frbx_event;
+
+/* A single pulse (Sec. 2.4.1 step d; Sec. 2.4.2 step d) after the DM merge of Sec. 5.3. */
+typedef struct frbx_cand {
+  int32_t series;  /* baseline index, or combination index */
+  int32_t dm_idx;  /* DM trial of highest power */
+  int32_t win_idx;
+  int32_t width;   /* window length in APs (characteristic width) */
+  int32_t k0;
+  int32_t sbd_idx, mbd_idx;
+  int32_t n_win;   /* distinct windows that saw it (step d) */
+  int32_t group;   /* cross-match group, or -1 (combined pulses, pre-merge lists) */
+  float amp;
+  float pnorm;     /* characteristic power */
+  int32_t reserved;
+  double t_s;      /* k0 * t_ap, seconds from the first AP */
+  double sbd_ns, mbd_ns;
+  double dm;
+} frbx_cand;
+
+/* A cross-matching group (Sec. 2.4.1): pulses of different baselines overlapping in time. */
+typedef struct frbx_group {
+  uint64_t bl_mask;
+  int32_t n_baselines;
+  int32_t n_pulses;
+} frbx_group;
+
+/*
+ * Outputs of frbx_search.  Each array is caller-owned with capacity *_cap
+ * elements (0 = not wanted; the pointer may then be NULL).  Every *_count is
+ * always set to the number of elements the full result has; if a count exceeds
+ * its capacity the first *_cap elements are written and frbx_search returns
+ * FRBX_ETRUNC after finishing everything else.
+ *
+ *  pulses      per-baseline single pulses after the DM merge, baseline ascending,
+ *              then in order of discovery; .group indexes groups[].
+ *  groups      cross-match groups in creation order.
+ *  combined    pulses of the power-summation scheme, combination ascending.
+ *  pulses_dm   optional: per-(baseline, DM) pulses before the DM merge.
+ *  events      optional: all threshold crossings of baselines then combinations,
+ *              ordered by (series, dm, window, k0).
+ *  series      optional per-segment fits, frbx_seg[n_bl][n_dm][S_tot] (layout from
+ *              frbx_series_layout; unused slots hold amp = -1).  Host or device
+ *              memory per series_on_device.
+ *  pnorm       optional normalised power, float[n_bl][n_dm][S_tot] (unused slots 0),
+ *              same memory kind as series.
+ */
+typedef struct frbx_results {
+  frbx_cand *pulses;
+  int64_t pulses_cap, pulses_count;
+  frbx_group *groups;
+  int64_t groups_cap, groups_count;
+  frbx_cand *combined;
+  int64_t combined_cap, combined_count;
+  frbx_cand *pulses_dm;
+  int64_t pulses_dm_cap, pulses_dm_count;
+  frbx_event *events;
+  int64_t events_cap, events_count;
+  frbx_seg *series;
+  float *pnorm;
+  int32_t series_on_device;
+  int32_t reserved;
+  int64_t series_cap, series_count;
+  int64_t events_baseline_count; /* out: the first this-many events are the baselines' */
+} frbx_results;
+
+/* Fill *p with the paper's defaults (threshold 3, N_win,min 3, whole grids, no combos). */
+void frbx_default_params(frbx_params *p);
+
+/*
+ * Create a handle for one setup on the current CUDA device.  Validates the
+ * setup, builds the frequency, MBD-grid, rotation and twiddle tables (FP64 on
+ * the host, rounded to FP32 once) and uploads them.
+ * Errors: FRBX_EINVAL, FRBX_ENOMEM, FRBX_ECUDA.  *out is NULL on error.
+ */
+int frbx_create(const frbx_setup *setup, frbx_handle **out);
+
+/* Release the handle and its device memory.  NULL is ignored. */
+void frbx_destroy(frbx_handle *h);
+
+/* Message of the last failed call on h (never NULL; "" if none). */
+const char *frbx_last_error(const frbx_handle *h);
+
+/* Grid sizes chosen at create time: Ls, Lm, df_grid (MHz) and g_n ([n_chan], may be NULL). */
+int frbx_grid_info(const frbx_handle *h, int32_t *Ls, int32_t *Lm, double *df_grid_mhz,
+                   int32_t *g_out);
+
+/*
+ * Eq. 1-2: dk[d][c] = floor(0.5 + 4.15e6 * DM_d * (f_c^-2 - f_ref^-2) / t_ap), computed on
+ * the device in FP64 in the order a = 4.15e6*DM; b = 1/(f*f) - 1/(fref*fref); dt = a*b;
+ * x = dt/t_ap; floor(0.5 + x), each step correctly rounded (no contraction).
+ *  dm       [n_dm] host, pc cm^-3, >= 0.
+ *  dk_out   [n_dm][n_chan*n_point] int32, host.
+ * Errors: FRBX_EINVAL, FRBX_ECUDA.
+ */
+int frbx_shift_table(frbx_handle *h, const double *dm, int32_t n_dm, int32_t *dk_out,
+                     void *cuda_stream);
+
+/*
+ * Series layout for T APs and a window list: for window w, segment s starts at
+ * k0 = s * step(l_w), step(l) = max(1, l/2) (half overlap, Sec. 2.4.1), and sits
+ * at slot offset[w] + s of a (baseline, DM) series of S_tot slots.
+ *  offset   [n_win] out (may be NULL); returns S_tot (or a negative error).
+ */
+int64_t frbx_series_layout(int32_t T, const int32_t *windows, int32_t n_win, int64_t *offset);
+
+/*
+ * The whole hot path (Sec. 2.2 - 2.4, Sec. 5.1, Sec. 5.3):
+ *  1. dispersion shift table for the DM grid (Eq. 1-2);
+ *  2. every valid half-overlapped segment of every window, baseline and DM:
+ *     dedispersed sum (Eq. 3), calibration rotation, 2-D delay transform on the
+ *     SBD x MBD grid (Eq. 5, Sec. 5.1) and its maximum;  a segment is valid when
+ *     k0 + max_c dk(d, c) + l <= T;
+ *  3. normalised power per (baseline, DM, window) over the valid segments (Eq. 6)
+ *     and the threshold;
+ *  4. steps b-d per (baseline, DM), the DM merge, cross-matching (Sec. 2.4.1);
+ *  5. for each baseline combination, summed amplitudes, Eq. 6, threshold, steps b
+ *     and d (no MBD step) and the DM merge (Sec. 2.4.2).
+ *
+ *  vis      complex64 cross spectra [n_bl][T][n_chan*n_point] (interleaved re, im
+ *           floats, row-major, 8-byte aligned).  If vis_on_device is nonzero it
+ *           is a device pointer, else a host pointer (copied to the device inside
+ *           the call; pinned memory is fastest).
+ *  n_bl     1..64 baselines;  T  APs (>= 1).
+ *  dm       [n_dm] host, DM trials (pc cm^-3), >= 0.
+ *  windows  [n_win] host, distinct window lengths in APs (>= 1), 1..16 of them.
+ *  params   search parameters (NULL = defaults).
+ *  res      outputs, see frbx_results.
+ * Errors: FRBX_EINVAL, FRBX_ENOMEM, FRBX_ECUDA, FRBX_ETRUNC, FRBX_EUNSUPPORTED.
+ */
+int frbx_search(frbx_handle *h, const void *vis, int32_t vis_on_device, int32_t n_bl, int32_t T,
+                const double *dm, int32_t n_dm, const int32_t *windows, int32_t n_win,
+                const frbx_params *params, frbx_results *res, void *cuda_stream);
+
+/*
+ * Stage entry point: fit an explicit list of segments (Eq. 3, Eq. 5, Sec. 5.1) with the
+ * kernels frbx_search uses, e.g. to check sampled segments of a large run.
+ *  vis, vis_on_device, n_bl, T, dm, n_dm   as in frbx_search.
+ *  segs     host int32 [n_seg][4] rows (bl, dm_idx, l, k0); each must satisfy
+ *           0 <= bl < n_bl, 0 <= dm_idx < n_dm, l >= 1, k0 >= 0 and
+ *           k0 + max_c dk(dm_idx, c) + l <= T (checked; FRBX_EINVAL otherwise).
+ *  out      host frbx_seg [n_seg].
+ * Errors: FRBX_EINVAL, FRBX_ENOMEM, FRBX_ECUDA, FRBX_EUNSUPPORTED.
+ */
+int frbx_fit_segments(frbx_handle *h, const void *vis, int32_t vis_on_device, int32_t n_bl,
+                      int32_t T, const double *dm, int32_t n_dm, const int32_t *segs,
+                      int64_t n_seg, const frbx_params *params, frbx_seg *out, void *cuda_stream);
+
+/*
+ * Host stage entry point (no GPU needed): single-pulse extraction from a list of
+ * threshold crossings, i.e. steps b-d of Sec. 2.4.1 per (series, DM), the DM merge of
+ * Sec. 5.3 per series and, if cross_match is nonzero, cross-matching of the series
+ * as baselines (Sec. 2.4.1).  frbx_search runs exactly this code on its events.
+ *  events     [n_events] ordered by (series, dm_idx, win_idx, k0) ascending (checked).
+ *  n_series   number of series (baselines or combinations); series < n_series < 64.
+ *  T, n_dm    scan length in APs and DM-trial count (event indices must be below them).
+ *  windows    [n_win] distinct window lengths (the events' win_idx index them).
+ *  Lm         MBD grid size for step c (angle 2 pi mbd_idx / Lm); 0 skips step c (the
+ *             power-summation scheme, Sec. 2.4.2).
+ *  nwin_min   N_win,min of step d.
+ *  pulses     out, DM-merged pulses (cap / *count as in frbx_results); the double fields
+ *             (t_s, sbd_ns, mbd_ns, dm) are left 0.
+ *  groups     out, cross-match groups (ignored when cross_match is 0).
+ *  pre_merge  out, per-(series, DM) pulses before the merge.
+ * Errors: FRBX_EINVAL, FRBX_ETRUNC.
+ */
+int frbx_extract_events(const frbx_event *events, int64_t n_events, int32_t n_series, int32_t T,
+                        int32_t n_dm, const int32_t *windows, int32_t n_win, int32_t Lm,
+                        int32_t nwin_min, int32_t cross_match, frbx_cand *pulses,
+                        int64_t pulses_cap, int64_t *pulses_count, frbx_group *groups,
+                        int64_t groups_cap, int64_t *groups_count, frbx_cand *pre_merge,
+                        int64_t pre_cap, int64_t *pre_count);
+
+/*
+ * Stage times of the last frbx_search on h, from CUDA events recorded on the call's
+ * stream (device time between the events) and, for the host stage, the host clock:
+ *  [0] shift table (Eq. 1-2)        [1] segment fit kernel (Eq. 3, Eq. 5, Sec. 5.1)
+ *  [2] baselines: Eq. 6 + threshold  [3] combinations: sum + Eq. 6 + threshold
+ *  [4] host extraction (Sec. 2.4.1 b-d, Sec. 5.3 merge, cross-matching, Sec. 2.4.2)
+ *  ms_out  [n] out, milliseconds (stages that did not run report 0).
+ * Returns the number of stages written (min(n, 5)) or FRBX_EINVAL.
+ */
+int frbx_last_stage_times(const frbx_handle *h, double *ms_out, int32_t n);
+
+/* Number of kernel launches issued by the last frbx_search / frbx_fit_segments call. */
+int64_t frbx_last_launch_count(const frbx_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FRBX_H */

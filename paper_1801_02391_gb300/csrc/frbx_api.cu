@@ -1,0 +1,755 @@
+// C ABI of libfrbx: argument checking, setup tables, scratch management and the
+// orchestration of the hot path (shift table -> fit -> normalise/threshold -> host
+// extraction).  Declarations and the contract of every entry point: include/frbx.h.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "frbx_internal.h"
+
+using frbx::FitArgs;
+using frbx::StatsArgs;
+
+namespace {
+
+int fail(frbx_handle *h, int code, const std::string &msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+int cuda_fail(frbx_handle *h, cudaError_t e, const char *what) {
+  const int code = (e == cudaErrorMemoryAllocation) ? FRBX_ENOMEM : FRBX_ECUDA;
+  cudaGetLastError();  // clear a sticky-free error so the next call starts clean
+  return fail(h, code, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define FRBX_CK(h, call)                                        \
+  do {                                                          \
+    cudaError_t e_ = (call);                                    \
+    if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);    \
+  } while (0)
+
+// Grow a scratch buffer to at least `bytes` (contents are not kept).
+cudaError_t ensure(frbx_handle::Buf &b, size_t bytes) {
+  if (b.bytes >= bytes && b.p) return cudaSuccess;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  const size_t want = std::max<size_t>(bytes, 256);
+  cudaError_t e = cudaMalloc(&b.p, want);
+  if (e == cudaSuccess) b.bytes = want;
+  return e;
+}
+
+template <class T>
+cudaError_t upload(T **dst, const std::vector<T> &src) {
+  cudaError_t e = cudaMalloc((void **)dst, std::max<size_t>(1, src.size()) * sizeof(T));
+  if (e != cudaSuccess) return e;
+  if (src.empty()) return cudaSuccess;
+  return cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
+
+int next_pow2(int v) {
+  int p = 1;
+  while (p < v) p *= 2;
+  return p;
+}
+
+int ilog2(int v) {
+  int r = 0;
+  while ((1 << r) < v) ++r;
+  return r;
+}
+
+int window_step(int l) { return std::max(1, l / 2); }
+
+int n_slots(int T, int l) { return T >= l ? (T - l) / window_step(l) + 1 : 0; }
+
+int n_valid(int T, int l, int dk_max) {
+  const long long r = (long long)T - dk_max - l;
+  return r >= 0 ? (int)(r / window_step(l) + 1) : 0;
+}
+
+// A delay window as the wrapped index interval [lo, lo + len) of an axis of L cells
+// whose value is v(s) for the signed index s = i (i < L/2) or i - L.
+template <class F>
+bool axis_window(int L, const double win[2], F value, int *lo, int *len) {
+  if (!(win[0] <= win[1])) {
+    *lo = 0;
+    *len = L;
+    return true;
+  }
+  int s_lo = INT32_MAX, s_hi = INT32_MIN;
+  for (int s = -L / 2; s < L / 2; ++s) {
+    const double v = value(s);
+    if (v >= win[0] && v <= win[1]) {
+      s_lo = std::min(s_lo, s);
+      s_hi = std::max(s_hi, s);
+    }
+  }
+  if (s_lo > s_hi) return false;
+  *lo = ((s_lo % L) + L) % L;
+  *len = s_hi - s_lo + 1;
+  return true;
+}
+
+std::once_flag g_const_once;
+
+struct Layout {
+  std::vector<int> win_len, win_off, win_step, n_valid;  // n_valid [n_dm][n_win]
+  int S_tot = 0;
+};
+
+}  // namespace
+
+extern "C" {
+
+void frbx_default_params(frbx_params *p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->threshold = 3.0f;
+  p->nwin_min = 3;
+  p->sbd_win_ns[0] = 1.0;
+  p->sbd_win_ns[1] = -1.0;
+  p->mbd_win_ns[0] = 1.0;
+  p->mbd_win_ns[1] = -1.0;
+  p->combos = nullptr;
+  p->n_combo = 0;
+  p->kernel = 0;
+}
+
+int frbx_create(const frbx_setup *s, frbx_handle **out) {
+  if (!out) return FRBX_EINVAL;
+  *out = nullptr;
+  if (!s || !s->f0_mhz) return FRBX_EINVAL;
+  const int N = s->n_chan, J = s->n_point;
+  if (N < 1 || N > frbx::kMaxChan || J < 2 || J > frbx::kMaxPoint) return FRBX_EINVAL;
+  if (!(s->f_bw_mhz > 0) || !(s->t_ap_ms > 0) || !std::isfinite(s->f_bw_mhz) ||
+      !std::isfinite(s->t_ap_ms))
+    return FRBX_EINVAL;
+  auto *h = new frbx_handle();
+  h->N = N;
+  h->J = J;
+  h->C = N * J;
+  h->f_bw = s->f_bw_mhz;
+  h->t_ap = s->t_ap_ms;
+  h->f0.assign(s->f0_mhz, s->f0_mhz + N);
+  for (double v : h->f0) {
+    if (!(v > 0) || !std::isfinite(v)) {
+      delete h;
+      return FRBX_EINVAL;
+    }
+  }
+  // point frequencies f0_n + (j * f_bw) / J
+  h->f.resize((size_t)h->C);
+  double fmax = 0;
+  for (int n = 0; n < N; ++n)
+    for (int j = 0; j < J; ++j) {
+      const double f = h->f0[(size_t)n] + ((double)j * s->f_bw_mhz) / (double)J;
+      h->f[(size_t)n * J + j] = f;
+      fmax = std::max(fmax, f);
+    }
+  h->f_ref = s->f_ref_dm_mhz != 0.0 ? s->f_ref_dm_mhz : fmax;
+  if (!(h->f_ref >= fmax)) {
+    delete h;
+    return FRBX_EINVAL;  // a reference below the band would make negative shifts
+  }
+  // MBD grid: GCD of the channel offsets in whole kHz
+  const double fmin0 = *std::min_element(h->f0.begin(), h->f0.end());
+  std::vector<long long> off_khz((size_t)N);
+  long long gcd = 0;
+  for (int n = 0; n < N; ++n) {
+    const double o = (h->f0[(size_t)n] - fmin0) * 1000.0;
+    const double r = std::nearbyint(o);
+    if (std::fabs(o - r) > 1e-3) {
+      delete h;
+      return FRBX_EINVAL;
+    }
+    off_khz[(size_t)n] = (long long)r;
+    if (r != 0) gcd = std::gcd(gcd, (long long)r);
+  }
+  if (gcd == 0) gcd = (long long)std::nearbyint(s->f_bw_mhz * 1000.0);
+  if (gcd <= 0) {
+    delete h;
+    return FRBX_EINVAL;
+  }
+  h->df_grid = (double)gcd / 1000.0;
+  h->g.resize((size_t)N);
+  int gmax = 0;
+  for (int n = 0; n < N; ++n) {
+    const long long gv = off_khz[(size_t)n] / gcd;
+    if (gv > frbx::kMaxLm) {
+      delete h;
+      return FRBX_EUNSUPPORTED;
+    }
+    h->g[(size_t)n] = (int)gv;
+    gmax = std::max(gmax, (int)gv);
+  }
+  const int sp = s->sbd_pad ? s->sbd_pad : 2, mp = s->mbd_pad ? s->mbd_pad : 2;
+  if (sp < 1 || mp < 1) {
+    delete h;
+    return FRBX_EINVAL;
+  }
+  h->Ls = sp * J;
+  h->Lm = mp * next_pow2(gmax + 1);
+  if (!is_pow2(h->Ls) || !is_pow2(h->Lm) || h->Ls > frbx::kMaxLs || h->Lm > frbx::kMaxLm ||
+      (long long)h->Ls * h->Lm > (1LL << 20)) {
+    delete h;
+    return FRBX_EUNSUPPORTED;
+  }
+  h->J1 = (J + 31) / 32;
+  // weight x calibration rotation exp(-i[2 pi (f_j - f_bw/2) dtau0_n + dphi0_n]) (Eq. 5)
+  const double two_pi = 6.283185307179586476925286766559;
+  std::vector<float2> wrot((size_t)h->C);
+  for (int n = 0; n < N; ++n)
+    for (int j = 0; j < J; ++j) {
+      const int c = n * J + j;
+      const bool used = j > 0 && !(s->flag && s->flag[c]);
+      const double fj = ((double)j * s->f_bw_mhz) / (double)J;
+      const double dt = s->chan_delay_ns ? s->chan_delay_ns[n] : 0.0;
+      const double dp = s->chan_phase_rad ? s->chan_phase_rad[n] : 0.0;
+      const double ph = two_pi * (fj - s->f_bw_mhz / 2.0) * dt * 1e-3 + dp;
+      wrot[(size_t)c] = used ? make_float2((float)std::cos(ph), (float)-std::sin(ph))
+                             : make_float2(0.f, 0.f);
+    }
+  auto tw = [&](int L) {
+    std::vector<float2> t((size_t)L);
+    for (int k = 0; k < L; ++k)
+      t[(size_t)k] = make_float2((float)std::cos(two_pi * k / L), (float)-std::sin(two_pi * k / L));
+    return t;
+  };
+  std::vector<float2> tws = tw(h->Ls), twm = tw(h->Lm);
+  // FFT-kernel tables
+  std::vector<float2> sbd_tw, mbd_tw;
+  std::vector<int> slot;
+  if (h->Ls % 32 == 0 && h->Lm % 32 == 0) {
+    const int PS = h->Ls / 32, PM = h->Lm / 32, JP = h->J1 * 32;
+    sbd_tw.assign((size_t)PS * JP, make_float2(0.f, 0.f));
+    for (int m1 = 0; m1 < PS; ++m1)
+      for (int j = 0; j < J; ++j) sbd_tw[(size_t)m1 * JP + j] = tws[(size_t)(((long long)j * m1) % h->Ls)];
+    mbd_tw.resize((size_t)N * PM);
+    for (int n = 0; n < N; ++n)
+      for (int q1 = 0; q1 < PM; ++q1)
+        mbd_tw[(size_t)n * PM + q1] = twm[(size_t)(((long long)h->g[(size_t)n] * q1) % h->Lm)];
+    std::vector<std::vector<int>> res(32);
+    for (int n = 0; n < N; ++n) res[(size_t)(h->g[(size_t)n] % 32)].push_back(n);
+    h->occ = 1;
+    for (auto &r : res) h->occ = std::max(h->occ, (int)r.size());
+    slot.assign((size_t)32 * h->occ, -1);
+    for (int g2 = 0; g2 < 32; ++g2)
+      for (size_t o = 0; o < res[(size_t)g2].size(); ++o) slot[(size_t)g2 * h->occ + o] = res[(size_t)g2][o];
+  }
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = upload(&h->d_f, h->f);
+  if (e == cudaSuccess) e = upload(&h->d_wrot, wrot);
+  if (e == cudaSuccess) e = upload(&h->d_tw_s, tws);
+  if (e == cudaSuccess) e = upload(&h->d_tw_m, twm);
+  if (e == cudaSuccess) e = upload(&h->d_g, h->g);
+  if (e == cudaSuccess) e = upload(&h->d_sbd_tw, sbd_tw);
+  if (e == cudaSuccess) e = upload(&h->d_mbd_tw, mbd_tw);
+  if (e == cudaSuccess) e = upload(&h->d_slot, slot);
+  if (e == cudaSuccess) {
+    std::call_once(g_const_once, frbx::set_fft_constants);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) {
+    const int code = e == cudaErrorMemoryAllocation ? FRBX_ENOMEM : FRBX_ECUDA;
+    cudaGetLastError();
+    frbx_destroy(h);
+    return code;
+  }
+  *out = h;
+  return FRBX_OK;
+}
+
+void frbx_destroy(frbx_handle *h) {
+  if (!h) return;
+  void *ptrs[] = {h->d_f, h->d_wrot, h->d_tw_s, h->d_tw_m, h->d_g, h->d_sbd_tw, h->d_mbd_tw, h->d_slot};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  for (cudaEvent_t e : h->ev)
+    if (e) cudaEventDestroy(e);
+  frbx_handle::Buf *bufs[] = {&h->vis, &h->dk, &h->dk_max, &h->series, &h->pnorm, &h->stats,
+                              &h->counts, &h->offsets, &h->events, &h->small, &h->seglist, &h->masks};
+  for (auto *b : bufs)
+    if (b->p) cudaFree(b->p);
+  delete h;
+}
+
+const char *frbx_last_error(const frbx_handle *h) { return h ? h->err.c_str() : "null handle"; }
+
+int frbx_grid_info(const frbx_handle *h, int32_t *Ls, int32_t *Lm, double *df_grid_mhz,
+                   int32_t *g_out) {
+  if (!h) return FRBX_EINVAL;
+  if (Ls) *Ls = h->Ls;
+  if (Lm) *Lm = h->Lm;
+  if (df_grid_mhz) *df_grid_mhz = h->df_grid;
+  if (g_out)
+    for (int n = 0; n < h->N; ++n) g_out[n] = h->g[(size_t)n];
+  return FRBX_OK;
+}
+
+int64_t frbx_series_layout(int32_t T, const int32_t *windows, int32_t n_win, int64_t *offset) {
+  if (T < 1 || n_win < 1 || n_win > frbx::kMaxWin || !windows) return FRBX_EINVAL;
+  int64_t tot = 0;
+  for (int w = 0; w < n_win; ++w) {
+    if (windows[w] < 1) return FRBX_EINVAL;
+    if (offset) offset[w] = tot;
+    tot += n_slots(T, windows[w]);
+  }
+  return tot;
+}
+
+int64_t frbx_last_launch_count(const frbx_handle *h) { return h ? h->launches : -1; }
+
+}  // extern "C"
+
+namespace {
+
+// Shift table for dm[] into h->dk / h->dk_max; dk_max copied to host.
+int run_shift_table(frbx_handle *h, const double *dm, int n_dm, std::vector<int> *dk_max,
+                    cudaStream_t st) {
+  for (int d = 0; d < n_dm; ++d)
+    if (!(dm[d] >= 0) || !std::isfinite(dm[d])) return fail(h, FRBX_EINVAL, "DM trials must be finite and >= 0");
+  FRBX_CK(h, ensure(h->small, sizeof(double) * (size_t)n_dm + 4096));
+  FRBX_CK(h, ensure(h->dk, sizeof(int) * (size_t)n_dm * h->C));
+  FRBX_CK(h, ensure(h->dk_max, sizeof(int) * (size_t)n_dm));
+  double *d_dm = (double *)h->small.p;
+  FRBX_CK(h, cudaMemcpyAsync(d_dm, dm, sizeof(double) * n_dm, cudaMemcpyHostToDevice, st));
+  FRBX_CK(h, frbx::launch_shift_table(h->d_f, h->C, h->f_ref, d_dm, n_dm, h->t_ap, (int *)h->dk.p,
+                                      (int *)h->dk_max.p, st, &h->launches));
+  dk_max->resize((size_t)n_dm);
+  FRBX_CK(h, cudaMemcpyAsync(dk_max->data(), h->dk_max.p, sizeof(int) * n_dm, cudaMemcpyDeviceToHost, st));
+  FRBX_CK(h, cudaStreamSynchronize(st));
+  return FRBX_OK;
+}
+
+int check_params(frbx_handle *h, const frbx_params *p, int n_bl, FitArgs *a) {
+  if (!(p->threshold == p->threshold)) return fail(h, FRBX_EINVAL, "threshold is NaN");
+  if (p->nwin_min < 1) return fail(h, FRBX_EINVAL, "nwin_min must be >= 1");
+  if (p->n_combo < 0 || (p->n_combo > 0 && !p->combos)) return fail(h, FRBX_EINVAL, "bad combos");
+  for (int c = 0; c < p->n_combo; ++c) {
+    const uint64_t m = p->combos[c];
+    if (m == 0 || (n_bl < 64 && (m >> n_bl) != 0)) return fail(h, FRBX_EINVAL, "combo mask names a missing baseline");
+  }
+  const int J = h->J, Ls = h->Ls, Lm = h->Lm;
+  const double fbw = h->f_bw, dfg = h->df_grid;
+  if (!axis_window(Ls, p->sbd_win_ns, [&](int s) { return (((double)s * J) * 1000.0) / ((double)Ls * fbw); },
+                   &a->m_lo, &a->m_len))
+    return fail(h, FRBX_EINVAL, "SBD window holds no grid cell");
+  if (!axis_window(Lm, p->mbd_win_ns, [&](int s) { return ((double)s * 1000.0) / ((double)Lm * dfg); },
+                   &a->q_lo, &a->q_len))
+    return fail(h, FRBX_EINVAL, "MBD window holds no grid cell");
+  if (p->kernel < 0 || p->kernel > 2) return fail(h, FRBX_EINVAL, "kernel must be 0, 1 or 2");
+  if (p->kernel == 2 && !frbx::fft_supported(h->Ls, h->Lm, h->J))
+    return fail(h, FRBX_EUNSUPPORTED, "FFT kernel needs Ls and Lm multiples of 32");
+  return FRBX_OK;
+}
+
+void fill_fit_tables(frbx_handle *h, FitArgs *a, const float2 *vis, int T, int n_dm) {
+  a->vis = vis;
+  a->T = T;
+  a->C = h->C;
+  a->N = h->N;
+  a->J = h->J;
+  a->n_dm = n_dm;
+  a->dk = (const int *)h->dk.p;
+  a->wrot = h->d_wrot;
+  a->tw_s = h->d_tw_s;
+  a->tw_m = h->d_tw_m;
+  a->g = h->d_g;
+  a->Ls = h->Ls;
+  a->Lm = h->Lm;
+  a->log2Lm = ilog2(h->Lm);
+  a->slot = h->d_slot;
+  a->occ = h->occ;
+  a->sbd_tw = h->d_sbd_tw;
+  a->mbd_tw = h->d_mbd_tw;
+  a->J1 = h->J1;
+}
+
+int check_vis(frbx_handle *h, const void *vis, int vis_on_device, int n_bl, int T, cudaStream_t st,
+              const float2 **dvis) {
+  if (!vis) return fail(h, FRBX_EINVAL, "vis is NULL");
+  if (n_bl < 1 || n_bl > frbx::kMaxBl) return fail(h, FRBX_EINVAL, "n_bl must be 1..64");
+  if (T < 1) return fail(h, FRBX_EINVAL, "T must be >= 1");
+  if (((uintptr_t)vis & 7u) != 0) return fail(h, FRBX_EINVAL, "vis must be 8-byte aligned");
+  const size_t bytes = sizeof(float2) * (size_t)n_bl * T * h->C;
+  if (vis_on_device) {
+    *dvis = (const float2 *)vis;
+    return FRBX_OK;
+  }
+  FRBX_CK(h, ensure(h->vis, bytes));
+  FRBX_CK(h, cudaMemcpyAsync(h->vis.p, vis, bytes, cudaMemcpyHostToDevice, st));
+  *dvis = (const float2 *)h->vis.p;
+  return FRBX_OK;
+}
+
+void to_cand(const frbx_handle *h, const frbx::Pulse &p, const double *dm, const Layout &,
+             bool combined, frbx_cand *c) {
+  std::memset(c, 0, sizeof(*c));
+  c->series = p.series;
+  c->dm_idx = p.d;
+  c->win_idx = p.w;
+  c->width = p.l;
+  c->k0 = p.k0;
+  c->sbd_idx = combined ? 0 : p.m;
+  c->mbd_idx = combined ? 0 : p.q;
+  c->n_win = p.n_win;
+  c->group = p.group;
+  c->amp = p.amp;
+  c->pnorm = p.p;
+  c->t_s = (double)p.k0 * h->t_ap * 1e-3;
+  const int sm = p.m < h->Ls / 2 ? p.m : p.m - h->Ls;
+  const int sq = p.q < h->Lm / 2 ? p.q : p.q - h->Lm;
+  c->sbd_ns = combined ? 0.0 : (((double)sm * h->J) * 1000.0) / ((double)h->Ls * h->f_bw);
+  c->mbd_ns = combined ? 0.0 : ((double)sq * 1000.0) / ((double)h->Lm * h->df_grid);
+  c->dm = dm[p.d];
+}
+
+// Normalise + threshold + ordered events of n_series series (baselines or combos).
+int run_stats(frbx_handle *h, StatsArgs sa, cudaStream_t st, std::vector<frbx_event> *ev) {
+  const size_t ns = (size_t)sa.n_series * sa.n_dm * sa.n_win;
+  FRBX_CK(h, ensure(h->stats, sizeof(double) * 2 * ns));
+  FRBX_CK(h, ensure(h->counts, sizeof(int) * (ns + 1)));
+  FRBX_CK(h, ensure(h->offsets, sizeof(long long) * (ns + 1)));
+  sa.mean_std = (double *)h->stats.p;
+  sa.counts = (int *)h->counts.p;
+  sa.offsets = (long long *)h->offsets.p;
+  FRBX_CK(h, frbx::launch_stats_count(sa, st, &h->launches));
+  FRBX_CK(h, frbx::launch_scan(sa, st, &h->launches));
+  long long total = 0;
+  FRBX_CK(h, cudaMemcpyAsync(&total, sa.offsets + ns, sizeof(long long), cudaMemcpyDeviceToHost, st));
+  FRBX_CK(h, cudaStreamSynchronize(st));
+  ev->resize((size_t)total);
+  if (total == 0) return FRBX_OK;
+  FRBX_CK(h, ensure(h->events, sizeof(frbx_event) * (size_t)total));
+  sa.events = (frbx_event *)h->events.p;
+  FRBX_CK(h, frbx::launch_events(sa, st, &h->launches));
+  FRBX_CK(h, cudaMemcpyAsync(ev->data(), sa.events, sizeof(frbx_event) * (size_t)total,
+                             cudaMemcpyDeviceToHost, st));
+  FRBX_CK(h, cudaStreamSynchronize(st));
+  return FRBX_OK;
+}
+
+}  // namespace
+
+extern "C" int frbx_shift_table(frbx_handle *h, const double *dm, int32_t n_dm, int32_t *dk_out,
+                                void *cuda_stream) {
+  if (!h) return FRBX_EINVAL;
+  if (!dm || !dk_out || n_dm < 1) return fail(h, FRBX_EINVAL, "bad DM list or output");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  h->launches = 0;
+  std::vector<int> dkm;
+  int rc = run_shift_table(h, dm, n_dm, &dkm, st);
+  if (rc) return rc;
+  FRBX_CK(h, cudaMemcpyAsync(dk_out, h->dk.p, sizeof(int) * (size_t)n_dm * h->C, cudaMemcpyDeviceToHost, st));
+  FRBX_CK(h, cudaStreamSynchronize(st));
+  return FRBX_OK;
+}
+
+extern "C" int frbx_fit_segments(frbx_handle *h, const void *vis, int32_t vis_on_device, int32_t n_bl,
+                                 int32_t T, const double *dm, int32_t n_dm, const int32_t *segs,
+                                 int64_t n_seg, const frbx_params *params, frbx_seg *out,
+                                 void *cuda_stream) {
+  if (!h) return FRBX_EINVAL;
+  h->launches = 0;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (!dm || n_dm < 1 || n_seg < 0 || (n_seg > 0 && (!segs || !out)))
+    return fail(h, FRBX_EINVAL, "bad DM list, segment list or output");
+  frbx_params p;
+  if (params) p = *params; else frbx_default_params(&p);
+  FitArgs a{};
+  int rc = check_params(h, &p, n_bl, &a);
+  if (rc) return rc;
+  const float2 *dvis = nullptr;
+  rc = check_vis(h, vis, vis_on_device, n_bl, T, st, &dvis);
+  if (rc) return rc;
+  std::vector<int> dkm;
+  rc = run_shift_table(h, dm, n_dm, &dkm, st);
+  if (rc) return rc;
+  for (int64_t i = 0; i < n_seg; ++i) {
+    const int32_t *r = segs + 4 * i;
+    if (r[0] < 0 || r[0] >= n_bl || r[1] < 0 || r[1] >= n_dm || r[2] < 1 || r[3] < 0 ||
+        (long long)r[3] + dkm[(size_t)r[1]] + r[2] > T)
+      return fail(h, FRBX_EINVAL, "segment row " + std::to_string(i) + " reads outside the cube");
+  }
+  if (n_seg == 0) return FRBX_OK;
+  FRBX_CK(h, ensure(h->seglist, sizeof(int32_t) * 4 * (size_t)n_seg));
+  FRBX_CK(h, ensure(h->series, sizeof(frbx_seg) * (size_t)n_seg));
+  FRBX_CK(h, cudaMemcpyAsync(h->seglist.p, segs, sizeof(int32_t) * 4 * (size_t)n_seg, cudaMemcpyHostToDevice, st));
+  fill_fit_tables(h, &a, dvis, T, n_dm);
+  a.seg = (const int *)h->seglist.p;
+  a.n_seg = n_seg;
+  a.tile = 16;
+  a.out = (frbx_seg *)h->series.p;
+  cudaError_t e = frbx::launch_fit(a, n_bl, true, p.kernel, st, &h->launches);
+  if (e == cudaErrorInvalidConfiguration) return fail(h, FRBX_EUNSUPPORTED, "fit kernel does not fit this shape");
+  FRBX_CK(h, e);
+  FRBX_CK(h, cudaMemcpyAsync(out, h->series.p, sizeof(frbx_seg) * (size_t)n_seg, cudaMemcpyDeviceToHost, st));
+  FRBX_CK(h, cudaStreamSynchronize(st));
+  return FRBX_OK;
+}
+
+extern "C" int frbx_search(frbx_handle *h, const void *vis, int32_t vis_on_device, int32_t n_bl,
+                           int32_t T, const double *dm, int32_t n_dm, const int32_t *windows,
+                           int32_t n_win, const frbx_params *params, frbx_results *res,
+                           void *cuda_stream) {
+  if (!h) return FRBX_EINVAL;
+  h->launches = 0;
+  h->err.clear();
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (!res) return fail(h, FRBX_EINVAL, "results is NULL");
+  if (!dm || n_dm < 1) return fail(h, FRBX_EINVAL, "need at least one DM trial");
+  if (!windows || n_win < 1 || n_win > frbx::kMaxWin) return fail(h, FRBX_EINVAL, "need 1..16 windows");
+  for (int w = 0; w < n_win; ++w) {
+    if (windows[w] < 1) return fail(h, FRBX_EINVAL, "window lengths must be >= 1");
+    for (int v = 0; v < w; ++v)
+      if (windows[v] == windows[w]) return fail(h, FRBX_EINVAL, "window lengths must be distinct");
+  }
+  frbx_params p;
+  if (params) p = *params; else frbx_default_params(&p);
+  FitArgs a{};
+  int rc = check_params(h, &p, n_bl, &a);
+  if (rc) return rc;
+  for (double &v : h->stage_ms) v = 0.0;
+  for (cudaEvent_t &ev : h->ev)
+    if (!ev) FRBX_CK(h, cudaEventCreate(&ev));
+  const float2 *dvis = nullptr;
+  rc = check_vis(h, vis, vis_on_device, n_bl, T, st, &dvis);
+  if (rc) return rc;
+  std::vector<int> dkm;
+  FRBX_CK(h, cudaEventRecord(h->ev[0], st));
+  rc = run_shift_table(h, dm, n_dm, &dkm, st);
+  if (rc) return rc;
+  FRBX_CK(h, cudaEventRecord(h->ev[1], st));
+
+  // layout of a (baseline, DM) series and the valid-segment counts (host)
+  Layout L;
+  L.win_len.assign(windows, windows + n_win);
+  long long stot = 0;
+  for (int w = 0; w < n_win; ++w) {
+    L.win_off.push_back((int)stot);
+    L.win_step.push_back(window_step(windows[w]));
+    stot += n_slots(T, windows[w]);
+  }
+  if (stot > (1LL << 30)) return fail(h, FRBX_EUNSUPPORTED, "too many segments per series");
+  L.S_tot = (int)stot;
+  L.n_valid.resize((size_t)n_dm * n_win);
+  for (int d = 0; d < n_dm; ++d)
+    for (int w = 0; w < n_win; ++w) L.n_valid[(size_t)d * n_win + w] = n_valid(T, windows[w], dkm[(size_t)d]);
+  // small tables: win_len | win_off | win_step | n_valid | masks
+  std::vector<int> tab;
+  tab.insert(tab.end(), L.win_len.begin(), L.win_len.end());
+  tab.resize(frbx::kMaxWin, 0);
+  tab.insert(tab.end(), L.win_off.begin(), L.win_off.end());
+  tab.resize(2 * frbx::kMaxWin, 0);
+  tab.insert(tab.end(), L.win_step.begin(), L.win_step.end());
+  tab.resize(3 * frbx::kMaxWin, 0);
+  tab.insert(tab.end(), L.n_valid.begin(), L.n_valid.end());
+  FRBX_CK(h, ensure(h->small, sizeof(int) * tab.size() + 4096));
+  int *d_tab = (int *)h->small.p;
+  FRBX_CK(h, cudaMemcpyAsync(d_tab, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice, st));
+  const size_t n_series_el = (size_t)n_bl * n_dm * L.S_tot;
+  FRBX_CK(h, ensure(h->series, sizeof(frbx_seg) * n_series_el));
+
+  // fit every segment
+  fill_fit_tables(h, &a, dvis, T, n_dm);
+  a.n_win = n_win;
+  a.win_len = d_tab;
+  a.win_off = d_tab + frbx::kMaxWin;
+  a.n_valid = d_tab + 3 * frbx::kMaxWin;
+  a.S_tot = L.S_tot;
+  a.tile = 64;
+  a.out = (frbx_seg *)h->series.p;
+  FRBX_CK(h, cudaEventRecord(h->ev[2], st));
+  cudaError_t e = frbx::launch_fit(a, n_bl, false, p.kernel, st, &h->launches);
+  if (e == cudaErrorInvalidConfiguration) return fail(h, FRBX_EUNSUPPORTED, "fit kernel does not fit this shape");
+  FRBX_CK(h, e);
+  FRBX_CK(h, cudaEventRecord(h->ev[3], st));
+
+  // normalised power and threshold crossings of every baseline series
+  const bool want_p = res->pnorm && res->series_cap >= (int64_t)n_series_el;
+  float *pn = nullptr;
+  if (want_p) {
+    if (res->series_on_device) {
+      pn = res->pnorm;
+    } else {
+      FRBX_CK(h, ensure(h->pnorm, sizeof(float) * n_series_el));
+      pn = (float *)h->pnorm.p;
+    }
+    FRBX_CK(h, cudaMemsetAsync(pn, 0, sizeof(float) * n_series_el, st));
+  }
+  StatsArgs sa{};
+  sa.series = (const frbx_seg *)h->series.p;
+  sa.n_bl = n_bl;
+  sa.n_dm = n_dm;
+  sa.S_tot = L.S_tot;
+  sa.n_win = n_win;
+  sa.win_off = d_tab + frbx::kMaxWin;
+  sa.win_step = d_tab + 2 * frbx::kMaxWin;
+  sa.n_valid = d_tab + 3 * frbx::kMaxWin;
+  sa.threshold = (double)p.threshold;
+  sa.n_series = n_bl;
+  sa.masks = nullptr;
+  sa.pnorm = pn;
+  sa.series_base = 0;
+  std::vector<frbx_event> ev_bl, ev_cb;
+  rc = run_stats(h, sa, st, &ev_bl);
+  if (rc) return rc;
+  FRBX_CK(h, cudaEventRecord(h->ev[4], st));
+  if (p.n_combo > 0) {
+    FRBX_CK(h, ensure(h->masks, sizeof(uint64_t) * (size_t)p.n_combo));
+    FRBX_CK(h, cudaMemcpyAsync(h->masks.p, p.combos, sizeof(uint64_t) * p.n_combo, cudaMemcpyHostToDevice, st));
+    sa.masks = (const unsigned long long *)h->masks.p;
+    sa.n_series = p.n_combo;
+    sa.pnorm = nullptr;
+    rc = run_stats(h, sa, st, &ev_cb);
+    if (rc) return rc;
+  }
+  FRBX_CK(h, cudaEventRecord(h->ev[5], st));
+  FRBX_CK(h, cudaEventSynchronize(h->ev[5]));
+  {
+    float ms = 0.f;
+    const int pairs[4][2] = {{0, 1}, {2, 3}, {3, 4}, {4, 5}};
+    for (int k = 0; k < 4; ++k) {
+      FRBX_CK(h, cudaEventElapsedTime(&ms, h->ev[pairs[k][0]], h->ev[pairs[k][1]]));
+      h->stage_ms[k] = ms;
+    }
+  }
+  const auto host_t0 = std::chrono::steady_clock::now();
+
+  // host extraction (Sec. 2.4.1 b-d, Sec. 5.3 merge, cross-matching, Sec. 2.4.2)
+  frbx::ExtractConfig cfg{T, n_dm, n_win, p.nwin_min, h->Lm, L.win_len.data()};
+  std::vector<frbx::Pulse> pre, merged, comb;
+  std::vector<frbx::GroupOut> groups;
+  frbx::extract_pulses(cfg, ev_bl.data(), (int64_t)ev_bl.size(), n_bl, true, &pre, &merged);
+  frbx::cross_match(T, &merged, n_bl, &groups);
+  if (p.n_combo > 0)
+    frbx::extract_pulses(cfg, ev_cb.data(), (int64_t)ev_cb.size(), p.n_combo, false, nullptr, &comb);
+
+  h->stage_ms[4] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - host_t0).count();
+  bool trunc = false;
+  auto put_cands = [&](const std::vector<frbx::Pulse> &v, bool combined, frbx_cand *dst, int64_t cap,
+                       int64_t *count) {
+    *count = (int64_t)v.size();
+    if (cap > 0 && (int64_t)v.size() > cap) trunc = true;
+    if (!dst) return;
+    const int64_t n = std::min<int64_t>(cap, (int64_t)v.size());
+    for (int64_t i = 0; i < n; ++i) to_cand(h, v[(size_t)i], dm, L, combined, &dst[i]);
+  };
+  put_cands(merged, false, res->pulses, res->pulses_cap, &res->pulses_count);
+  put_cands(comb, true, res->combined, res->combined_cap, &res->combined_count);
+  put_cands(pre, false, res->pulses_dm, res->pulses_dm_cap, &res->pulses_dm_count);
+  res->groups_count = (int64_t)groups.size();
+  if (res->groups) {
+    const int64_t n = std::min<int64_t>(res->groups_cap, (int64_t)groups.size());
+    for (int64_t i = 0; i < n; ++i) {
+      res->groups[i].bl_mask = groups[(size_t)i].mask;
+      res->groups[i].n_baselines = groups[(size_t)i].n_baselines;
+      res->groups[i].n_pulses = groups[(size_t)i].n_pulses;
+    }
+  }
+  if (res->groups_cap > 0 && (int64_t)groups.size() > res->groups_cap) trunc = true;
+  res->events_count = (int64_t)(ev_bl.size() + ev_cb.size());
+  res->events_baseline_count = (int64_t)ev_bl.size();
+  if (res->events) {
+    int64_t k = 0;
+    for (const auto &ev : {&ev_bl, &ev_cb})
+      for (const frbx_event &x : *ev) {
+        if (k >= res->events_cap) break;
+        res->events[k++] = x;
+      }
+  }
+  if (res->events_cap > 0 && res->events_count > res->events_cap) trunc = true;
+  res->series_count = (int64_t)n_series_el;
+  if (res->series && res->series_cap >= (int64_t)n_series_el) {
+    FRBX_CK(h, cudaMemcpyAsync(res->series, h->series.p, sizeof(frbx_seg) * n_series_el,
+                               res->series_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  }
+  if (want_p && !res->series_on_device)
+    FRBX_CK(h, cudaMemcpyAsync(res->pnorm, pn, sizeof(float) * n_series_el, cudaMemcpyDeviceToHost, st));
+  if ((res->series || res->pnorm) && res->series_cap < (int64_t)n_series_el) trunc = true;
+  FRBX_CK(h, cudaStreamSynchronize(st));
+  if (trunc) return fail(h, FRBX_ETRUNC, "an output array was too small");
+  return FRBX_OK;
+}
+
+extern "C" int frbx_extract_events(const frbx_event *events, int64_t n_events, int32_t n_series,
+                                   int32_t T, int32_t n_dm, const int32_t *windows, int32_t n_win,
+                                   int32_t Lm, int32_t nwin_min, int32_t cross_match,
+                                   frbx_cand *pulses, int64_t pulses_cap, int64_t *pulses_count,
+                                   frbx_group *groups, int64_t groups_cap, int64_t *groups_count,
+                                   frbx_cand *pre_merge, int64_t pre_cap, int64_t *pre_count) {
+  if (n_events < 0 || (n_events > 0 && !events) || n_series < 1 || n_series > 64 || T < 1 || n_dm < 1 ||
+      !windows || n_win < 1 || n_win > frbx::kMaxWin || Lm < 0 || nwin_min < 1)
+    return FRBX_EINVAL;
+  for (int w = 0; w < n_win; ++w) {
+    if (windows[w] < 1) return FRBX_EINVAL;
+    for (int v = 0; v < w; ++v)
+      if (windows[v] == windows[w]) return FRBX_EINVAL;
+  }
+  for (int64_t i = 0; i < n_events; ++i) {
+    const frbx_event &e = events[i];
+    if (e.series < 0 || e.series >= n_series || e.dm_idx < 0 || e.dm_idx >= n_dm || e.win_idx < 0 ||
+        e.win_idx >= n_win || e.k0 < 0 || e.k0 >= T || (Lm > 0 && e.mbd_idx >= Lm))
+      return FRBX_EINVAL;
+    if (i > 0) {
+      const frbx_event &f = events[i - 1];
+      const long long a[4] = {f.series, f.dm_idx, f.win_idx, f.k0}, b[4] = {e.series, e.dm_idx, e.win_idx, e.k0};
+      if (!std::lexicographical_compare(a, a + 4, b, b + 4)) return FRBX_EINVAL;
+    }
+  }
+  frbx::ExtractConfig cfg{T, n_dm, n_win, nwin_min, Lm, windows};
+  std::vector<frbx::Pulse> pre, merged;
+  std::vector<frbx::GroupOut> gr;
+  frbx::extract_pulses(cfg, events, n_events, n_series, Lm > 0, &pre, &merged);
+  if (cross_match) frbx::cross_match(T, &merged, n_series, &gr);
+  bool trunc = false;
+  auto put = [&](const std::vector<frbx::Pulse> &v, frbx_cand *dst, int64_t cap, int64_t *count) {
+    if (count) *count = (int64_t)v.size();
+    if (cap > 0 && (int64_t)v.size() > cap) trunc = true;
+    if (!dst) return;
+    for (int64_t i = 0; i < std::min<int64_t>(cap, (int64_t)v.size()); ++i) {
+      const frbx::Pulse &p = v[(size_t)i];
+      frbx_cand &c = dst[i];
+      std::memset(&c, 0, sizeof(c));
+      c.series = p.series;
+      c.dm_idx = p.d;
+      c.win_idx = p.w;
+      c.width = p.l;
+      c.k0 = p.k0;
+      c.sbd_idx = p.m;
+      c.mbd_idx = p.q;
+      c.n_win = p.n_win;
+      c.group = p.group;
+      c.amp = p.amp;
+      c.pnorm = p.p;
+    }
+  };
+  put(merged, pulses, pulses_cap, pulses_count);
+  put(pre, pre_merge, pre_cap, pre_count);
+  if (groups_count) *groups_count = (int64_t)gr.size();
+  if (groups)
+    for (int64_t i = 0; i < std::min<int64_t>(groups_cap, (int64_t)gr.size()); ++i) {
+      groups[i].bl_mask = gr[(size_t)i].mask;
+      groups[i].n_baselines = gr[(size_t)i].n_baselines;
+      groups[i].n_pulses = gr[(size_t)i].n_pulses;
+    }
+  if (groups_cap > 0 && (int64_t)gr.size() > groups_cap) trunc = true;
+  return trunc ? FRBX_ETRUNC : FRBX_OK;
+}
+
+extern "C" int frbx_last_stage_times(const frbx_handle *h, double *ms_out, int32_t n) {
+  if (!h || !ms_out || n < 0) return FRBX_EINVAL;
+  const int k = std::min(n, 5);
+  for (int i = 0; i < k; ++i) ms_out[i] = h->stage_ms[i];
+  return k;
+}

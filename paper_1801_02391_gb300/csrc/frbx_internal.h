@@ -1,0 +1,130 @@
+// Internal declarations shared by the translation units of libfrbx.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/frbx.h"
+
+namespace frbx {
+
+// Largest supported shapes (see frbx_setup in frbx.h).
+constexpr int kMaxChan = 64;
+constexpr int kMaxPoint = 256;
+constexpr int kMaxLs = 1024;
+constexpr int kMaxLm = 4096;
+constexpr int kMaxWin = 16;
+constexpr int kMaxBl = 64;
+constexpr int kFitThreads = 256;
+
+// Segment source of a fit launch: either the implicit half-overlap layout of a
+// (baseline, DM) series, or an explicit device list of (bl, d, l, k0) rows.
+struct FitArgs {
+  const float2 *vis;       // [n_bl][T][C]
+  int T, C, N, J;
+  int n_dm;
+  const int *dk;           // [n_dm][C]
+  const float2 *wrot;      // [C]  weight x calibration rotation
+  const float2 *tw_s;      // [Ls] exp(-2 pi i k / Ls)
+  const float2 *tw_m;      // [Lm] exp(-2 pi i k / Lm)
+  const int *g;            // [N]
+  int Ls, Lm, log2Lm;
+  // delay windows as wrapped index intervals: m searched iff ((m - m_lo) & (Ls-1)) < m_len
+  int m_lo, m_len, q_lo, q_len;
+  // implicit layout
+  int n_win;
+  const int *win_len;      // [n_win]
+  const int *win_off;      // [n_win] slot offset within a series
+  const int *n_valid;      // [n_dm][n_win]
+  int S_tot;
+  int tile;                // slots per CTA
+  // explicit list
+  const int *seg;          // [n_seg][4]
+  long long n_seg;
+  frbx_seg *out;           // implicit: [n_bl][n_dm][S_tot]; list: [n_seg]
+  // FFT kernel tables
+  const int *slot;         // [32][occ] channel with g_n = g2 (mod 32), -1 = empty
+  int occ;
+  const float2 *sbd_tw;    // [Ls/32][J1*32] exp(-2 pi i (j m1 mod Ls)/Ls), zero for j >= J
+  const float2 *mbd_tw;    // [N][Lm/32] exp(-2 pi i (g_n q1 mod Lm)/Lm)
+  int J1;                  // ceil(J / 32)
+};
+
+// Launchers (kernels_fit.cu).  Return a cudaError_t.
+cudaError_t launch_fit(const FitArgs &a, int n_bl, bool list_mode, int kernel,
+                       cudaStream_t st, int64_t *launches);
+bool fft_supported(int Ls, int Lm, int J);
+void set_fft_constants();
+
+// kernels_misc.cu
+cudaError_t launch_shift_table(const double *f, int C, double fref, const double *dm, int n_dm,
+                               double t_ap, int *dk, int *dk_max, cudaStream_t st,
+                               int64_t *launches);
+
+struct StatsArgs {
+  const frbx_seg *series;  // [n_bl][n_dm][S_tot]
+  int n_bl, n_dm, S_tot, n_win;
+  const int *win_off;      // [n_win]
+  const int *n_valid;      // [n_dm][n_win]
+  const int *win_step;     // [n_win]
+  const unsigned long long *masks;  // [n_series] baseline masks, or null for plain baselines
+  int n_series;
+  double threshold;
+  double *mean_std;        // [n_series][n_dm][n_win][2]
+  int *counts;             // [n_series * n_dm * n_win + 1]
+  long long *offsets;      // [n_series * n_dm * n_win + 1]
+  frbx_event *events;      // output
+  float *pnorm;            // optional [n_series][n_dm][S_tot]
+  int series_base;         // value stored in frbx_event.series = series_base + s
+};
+cudaError_t launch_stats_count(const StatsArgs &a, cudaStream_t st, int64_t *launches);
+cudaError_t launch_scan(const StatsArgs &a, cudaStream_t st, int64_t *launches);
+cudaError_t launch_events(const StatsArgs &a, cudaStream_t st, int64_t *launches);
+
+// extract.cpp: host steps of Sec. 2.4 and Sec. 5.3
+struct ExtractConfig {
+  int T, n_dm, n_win, nwin_min, Lm;
+  const int *win_len;
+};
+struct Pulse {
+  int series, d, w, l, k0, m, q, n_win, group;
+  float amp, p;
+};
+struct GroupOut {
+  uint64_t mask;
+  int n_baselines, n_pulses;
+};
+// events: ordered by (series, d, w, k0).  Outputs per-(series, d) pulses (pre-merge) and
+// DM-merged pulses per series.
+void extract_pulses(const ExtractConfig &cfg, const frbx_event *ev, int64_t n_ev, int n_series,
+                    bool use_mbd, std::vector<Pulse> *pre_merge, std::vector<Pulse> *merged);
+void cross_match(int T, std::vector<Pulse> *merged, int n_bl, std::vector<GroupOut> *groups);
+
+}  // namespace frbx
+
+struct frbx_handle {
+  int device = 0;
+  int N = 0, J = 0, C = 0;
+  double f_bw = 0, t_ap = 0, f_ref = 0, df_grid = 0;
+  int Ls = 0, Lm = 0, occ = 0, J1 = 0;
+  std::vector<double> f0, f;
+  std::vector<int> g;
+  std::string err;
+  int64_t launches = 0;
+  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  double stage_ms[5] = {0, 0, 0, 0, 0};
+  // constant device tables
+  double *d_f = nullptr;
+  float2 *d_wrot = nullptr, *d_tw_s = nullptr, *d_tw_m = nullptr;
+  float2 *d_sbd_tw = nullptr, *d_mbd_tw = nullptr;
+  int *d_g = nullptr, *d_slot = nullptr;
+  // scratch, grown on demand
+  struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+  };
+  Buf vis, dk, dk_max, series, pnorm, stats, counts, offsets, events, small, seglist, masks;
+};
