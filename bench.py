@@ -145,6 +145,18 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x: float) -> float:
+    """Largest value of x over all ranks (identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def oracle_sample_rows(wl, dk_max, n_dm_s, ts):
     """Segments of baseline 0, n_dm_s DM trials spread over the grid, APs [0, ts)."""
     from oracle import reference as R
@@ -264,11 +276,7 @@ def main():
     clocks = clk.stop()
     ms = ev0.elapsed_time(ev1) / args.steps
     stages = h.stage_times()
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms)
     value = world * cells / (ms / 1e3)
 
     # end to end through the public API from pinned host memory
@@ -285,12 +293,7 @@ def main():
         e2e_ms.append(e0.elapsed_time(e1))
         d2h = 4 * len(wl.dms) + 16 + 28 * o["counts"]["events_baseline"] + \
             28 * (o["counts"]["events"] - o["counts"]["events_baseline"]) + 16 * (1 + len(combos))
-    e2e = statistics.mean(e2e_ms)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e = float(t.item())
+    e2e = max_over_ranks(statistics.mean(e2e_ms))
 
     flops = n_seg * fft_flops_per_segment(wl.n_chan, h.Ls, h.Lm)
     fit_mean = statistics.mean(fit_ms)

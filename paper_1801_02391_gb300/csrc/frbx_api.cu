@@ -135,6 +135,8 @@ int frbx_create(const frbx_setup *s, frbx_handle **out) {
       !std::isfinite(s->t_ap_ms))
     return FRBX_EINVAL;
   auto *h = new frbx_handle();
+  for (auto &row : h->slot_n)
+    for (short &v : row) v = -1;
   h->N = N;
   h->J = J;
   h->C = N * J;
@@ -245,6 +247,9 @@ int frbx_create(const frbx_setup *s, frbx_handle **out) {
     slot.assign((size_t)32 * h->occ, -1);
     for (int g2 = 0; g2 < 32; ++g2)
       for (size_t o = 0; o < res[(size_t)g2].size(); ++o) slot[(size_t)g2 * h->occ + o] = res[(size_t)g2][o];
+    for (int g2 = 0; g2 < 32; ++g2)
+      for (int o = 0; o < 4; ++o)
+        h->slot_n[g2][o] = (short)(o < (int)res[(size_t)g2].size() ? res[(size_t)g2][(size_t)o] : -1);
   }
   cudaError_t e = cudaGetDevice(&h->device);
   if (e == cudaSuccess) e = upload(&h->d_f, h->f);
@@ -373,6 +378,7 @@ void fill_fit_tables(frbx_handle *h, FitArgs *a, const float2 *vis, int T, int n
   a->sbd_tw = h->d_sbd_tw;
   a->mbd_tw = h->d_mbd_tw;
   a->J1 = h->J1;
+  std::memcpy(a->slot_n, h->slot_n, sizeof(a->slot_n));
 }
 
 int check_vis(frbx_handle *h, const void *vis, int vis_on_device, int n_bl, int T, cudaStream_t st,

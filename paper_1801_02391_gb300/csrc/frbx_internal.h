@@ -51,6 +51,7 @@ struct FitArgs {
   const float2 *sbd_tw;    // [Ls/32][J1*32] exp(-2 pi i (j m1 mod Ls)/Ls), zero for j >= J
   const float2 *mbd_tw;    // [N][Lm/32] exp(-2 pi i (g_n q1 mod Lm)/Lm)
   int J1;                  // ceil(J / 32)
+  short slot_n[32][4];     // FFT kernel: channel n with g_n = g2 (mod 32), occupancy o; -1 = none
 };
 
 // Launchers (kernels_fit.cu).  Return a cudaError_t.
@@ -58,6 +59,11 @@ cudaError_t launch_fit(const FitArgs &a, int n_bl, bool list_mode, int kernel,
                        cudaStream_t st, int64_t *launches);
 bool fft_supported(int Ls, int Lm, int J);
 void set_fft_constants();
+// kernels_fft.cu
+cudaError_t launch_fit_fft(const FitArgs &a, int n_bl, bool list_mode, cudaStream_t st,
+                           int64_t *launches);
+size_t max_smem_optin();
+bool fit_grid(const FitArgs &a, int n_bl, bool list_mode, dim3 *grid);
 
 // kernels_misc.cu
 cudaError_t launch_shift_table(const double *f, int C, double fref, const double *dm, int n_dm,
@@ -110,6 +116,7 @@ struct frbx_handle {
   int N = 0, J = 0, C = 0;
   double f_bw = 0, t_ap = 0, f_ref = 0, df_grid = 0;
   int Ls = 0, Lm = 0, occ = 0, J1 = 0;
+  short slot_n[32][4];  // channel of residue class g2 (mod 32), occupancy o; -1 = none
   std::vector<double> f0, f;
   std::vector<int> g;
   std::string err;

@@ -96,6 +96,15 @@ def test_fit_short_channels_padded_fft(frbx, kernel):
     _fit_case(frbx, wl, kernel=kernel, n=150, seed=2)
 
 
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_fit_crowded_residue_classes(frbx, kernel):
+    """Channels whose MBD grid indices collide modulo 32 (g = 0, 32, 64, 96 share a class):
+    the FFT kernel's inner sum over up to four channels per class."""
+    wl = synth.make_tiny(n_chan=7, n_point=32, T=120, n_bl=2, dms=(0.0, 50.0), windows=(1, 2, 4),
+                         f0=500.0 + 4.0 * np.array([0, 32, 64, 96, 1, 33, 70]), f_bw=4.0)
+    _fit_case(frbx, wl, kernel=kernel, n=120, seed=4)
+
+
 def test_fit_tiny_irregular_direct(frbx):
     wl = synth.make_tiny(seed_offset=3)
     _fit_case(frbx, wl, kernel=0, n=100, seed=3)
