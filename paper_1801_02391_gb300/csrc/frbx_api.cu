@@ -251,6 +251,40 @@ int frbx_create(const frbx_setup *s, frbx_handle **out) {
       for (int o = 0; o < 4; ++o)
         h->slot_n[g2][o] = (short)(o < (int)res[(size_t)g2].size() ? res[(size_t)g2][(size_t)o] : -1);
   }
+  // BF16 DFT matrix of the MBD transform for the tensor-core fit, in its shared-memory image
+  // (rows: chunks of NC output columns, first half Re G, second half Im G; K-major, 64-wide
+  // K atoms, 128-byte swizzle); phases from the exact index g_n q mod Lm, cos/sin in FP64
+  std::vector<uint16_t> bimg;
+  if (frbx::mma_supported(h->Ls, h->Lm, N, J)) {
+    const int KA = (2 * N + 63) / 64, rows = 2 * h->Lm, NC = std::min(256, rows), half = NC / 2;
+    bimg.assign((size_t)KA * rows * 64, 0);
+    auto bf16 = [](double v) {
+      const float f = (float)v;
+      uint32_t u;
+      std::memcpy(&u, &f, 4);
+      u += 0x7FFFu + ((u >> 16) & 1u);  // round to nearest even
+      return (uint16_t)(u >> 16);
+    };
+    auto put = [&](int R, int k, double v) {
+      const size_t off = (size_t)(k / 64) * rows * 128 + (size_t)(R / 8) * 1024 + (size_t)(R % 8) * 128 +
+                         (size_t)((((k % 64) / 8) ^ (R % 8)) * 16) + (size_t)(k % 8) * 2;
+      bimg[off / 2] = bf16(v);
+    };
+    for (int R = 0; R < rows; ++R) {
+      const int c = R / NC, r = R % NC, q = c * half + (r % half);
+      const bool im = r >= half;
+      for (int n = 0; n < N; ++n) {
+        const long long ex = ((long long)h->g[(size_t)n] * q) % h->Lm;
+        const double th = two_pi * (double)ex / (double)h->Lm;
+        put(R, n, im ? -std::sin(th) : std::cos(th));
+        put(R, N + n, im ? std::cos(th) : std::sin(th));
+      }
+    }
+    h->KA = KA;
+    h->NC = NC;
+    h->b_atom_bytes = rows * 128;
+    h->b_bytes = KA * rows * 128;
+  }
   cudaError_t e = cudaGetDevice(&h->device);
   if (e == cudaSuccess) e = upload(&h->d_f, h->f);
   if (e == cudaSuccess) e = upload(&h->d_wrot, wrot);
@@ -260,6 +294,7 @@ int frbx_create(const frbx_setup *s, frbx_handle **out) {
   if (e == cudaSuccess) e = upload(&h->d_sbd_tw, sbd_tw);
   if (e == cudaSuccess) e = upload(&h->d_mbd_tw, mbd_tw);
   if (e == cudaSuccess) e = upload(&h->d_slot, slot);
+  if (e == cudaSuccess && !bimg.empty()) e = upload((uint16_t **)&h->d_bimg, bimg);
   if (e == cudaSuccess) {
     std::call_once(g_const_once, frbx::set_fft_constants);
     e = cudaGetLastError();
@@ -276,13 +311,14 @@ int frbx_create(const frbx_setup *s, frbx_handle **out) {
 
 void frbx_destroy(frbx_handle *h) {
   if (!h) return;
-  void *ptrs[] = {h->d_f, h->d_wrot, h->d_tw_s, h->d_tw_m, h->d_g, h->d_sbd_tw, h->d_mbd_tw, h->d_slot};
+  void *ptrs[] = {h->d_f, h->d_wrot, h->d_tw_s, h->d_tw_m, h->d_g, h->d_sbd_tw, h->d_mbd_tw, h->d_slot, h->d_bimg};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : h->ev)
     if (e) cudaEventDestroy(e);
   frbx_handle::Buf *bufs[] = {&h->vis, &h->dk, &h->dk_max, &h->series, &h->pnorm, &h->stats,
-                              &h->counts, &h->offsets, &h->events, &h->small, &h->seglist, &h->masks};
+                              &h->counts, &h->offsets, &h->events, &h->small, &h->seglist, &h->masks,
+                              &h->prefix, &h->errflag};
   for (auto *b : bufs)
     if (b->p) cudaFree(b->p);
   delete h;
@@ -352,7 +388,12 @@ int check_params(frbx_handle *h, const frbx_params *p, int n_bl, FitArgs *a) {
   if (!axis_window(Lm, p->mbd_win_ns, [&](int s) { return ((double)s * 1000.0) / ((double)Lm * dfg); },
                    &a->q_lo, &a->q_len))
     return fail(h, FRBX_EINVAL, "MBD window holds no grid cell");
-  if (p->kernel < 0 || p->kernel > 2) return fail(h, FRBX_EINVAL, "kernel must be 0, 1 or 2");
+  if (p->kernel < 0 || p->kernel > 3) return fail(h, FRBX_EINVAL, "kernel must be 0, 1, 2 or 3");
+  if (p->kernel == 3) {
+    if (!h->d_bimg) return fail(h, FRBX_EUNSUPPORTED, "tensor-core fit needs Ls of 64 or 128, 2 Lm >= 32, N <= 64");
+    if (a->m_len != Ls || a->q_len != Lm)
+      return fail(h, FRBX_EUNSUPPORTED, "tensor-core fit searches the whole grid (no delay windows)");
+  }
   if (p->kernel == 2 && !frbx::fft_supported(h->Ls, h->Lm, h->J))
     return fail(h, FRBX_EUNSUPPORTED, "FFT kernel needs Ls and Lm multiples of 32");
   return FRBX_OK;
@@ -418,6 +459,44 @@ void to_cand(const frbx_handle *h, const frbx::Pulse &p, const double *dm, const
   c->sbd_ns = combined ? 0.0 : (((double)sm * h->J) * 1000.0) / ((double)h->Ls * h->f_bw);
   c->mbd_ns = combined ? 0.0 : ((double)sq * 1000.0) / ((double)h->Lm * h->df_grid);
   c->dm = dm[p.d];
+}
+
+// Tensor-core fit of n_valid segments (implicit layout when prefix is non-empty, else list).
+int run_fit_mma(frbx_handle *h, const FitArgs &a, int n_bl, bool list_mode, long long n_valid,
+                const std::vector<long long> &prefix, cudaStream_t st) {
+  frbx::MmaArgs mm{};
+  mm.bimg = h->d_bimg;
+  mm.b_bytes = h->b_bytes;
+  mm.b_atom_bytes = h->b_atom_bytes;
+  mm.KA = h->KA;
+  mm.NC = h->NC;
+  mm.n_chunk = 2 * h->Lm / h->NC;
+  mm.kk_steps = (2 * h->N + 15) / 16;
+  int cols = 32;
+  while (cols < 2 * h->NC) cols *= 2;
+  mm.tmem_cols = cols;
+  mm.spt = 128 / h->Ls;
+  mm.n_valid = n_valid;
+  mm.timeout = 2000000000LL;
+  if (!list_mode) {
+    FRBX_CK(h, ensure(h->prefix, sizeof(long long) * prefix.size()));
+    FRBX_CK(h, cudaMemcpyAsync(h->prefix.p, prefix.data(), sizeof(long long) * prefix.size(),
+                               cudaMemcpyHostToDevice, st));
+    mm.prefix = (const long long *)h->prefix.p;
+    mm.n_prefix = (int)prefix.size();
+    mm.per_bl = prefix.back();
+  }
+  FRBX_CK(h, ensure(h->errflag, sizeof(int)));
+  FRBX_CK(h, cudaMemsetAsync(h->errflag.p, 0, sizeof(int), st));
+  mm.err = (int *)h->errflag.p;
+  cudaError_t e = frbx::launch_fit_mma(a, mm, n_bl, list_mode, st, &h->launches);
+  if (e == cudaErrorInvalidConfiguration) return fail(h, FRBX_EUNSUPPORTED, "tensor-core fit does not fit this shape");
+  FRBX_CK(h, e);
+  int flag = 0;
+  FRBX_CK(h, cudaMemcpyAsync(&flag, h->errflag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  FRBX_CK(h, cudaStreamSynchronize(st));
+  if (flag) return fail(h, FRBX_ETIMEOUT, "tensor-core fit: a bounded wait gave up");
+  return FRBX_OK;
 }
 
 // Normalise + threshold + ordered events of n_series series (baselines or combos).
@@ -496,9 +575,14 @@ extern "C" int frbx_fit_segments(frbx_handle *h, const void *vis, int32_t vis_on
   a.n_seg = n_seg;
   a.tile = 16;
   a.out = (frbx_seg *)h->series.p;
-  cudaError_t e = frbx::launch_fit(a, n_bl, true, p.kernel, st, &h->launches);
-  if (e == cudaErrorInvalidConfiguration) return fail(h, FRBX_EUNSUPPORTED, "fit kernel does not fit this shape");
-  FRBX_CK(h, e);
+  if (p.kernel == 3) {
+    rc = run_fit_mma(h, a, n_bl, true, n_seg, {}, st);
+    if (rc) return rc;
+  } else {
+    cudaError_t e = frbx::launch_fit(a, n_bl, true, p.kernel, st, &h->launches);
+    if (e == cudaErrorInvalidConfiguration) return fail(h, FRBX_EUNSUPPORTED, "fit kernel does not fit this shape");
+    FRBX_CK(h, e);
+  }
   FRBX_CK(h, cudaMemcpyAsync(out, h->series.p, sizeof(frbx_seg) * (size_t)n_seg, cudaMemcpyDeviceToHost, st));
   FRBX_CK(h, cudaStreamSynchronize(st));
   return FRBX_OK;
@@ -576,9 +660,17 @@ extern "C" int frbx_search(frbx_handle *h, const void *vis, int32_t vis_on_devic
   a.tile = 64;
   a.out = (frbx_seg *)h->series.p;
   FRBX_CK(h, cudaEventRecord(h->ev[2], st));
-  cudaError_t e = frbx::launch_fit(a, n_bl, false, p.kernel, st, &h->launches);
-  if (e == cudaErrorInvalidConfiguration) return fail(h, FRBX_EUNSUPPORTED, "fit kernel does not fit this shape");
-  FRBX_CK(h, e);
+  if (p.kernel == 3) {
+    std::vector<long long> prefix((size_t)n_dm * n_win + 1, 0);
+    for (size_t i = 0; i < L.n_valid.size(); ++i) prefix[i + 1] = prefix[i] + L.n_valid[i];
+    FRBX_CK(h, cudaEventRecord(h->ev[2], st));
+    rc = run_fit_mma(h, a, n_bl, false, prefix.back() * n_bl, prefix, st);
+    if (rc) return rc;
+  } else {
+    cudaError_t e = frbx::launch_fit(a, n_bl, false, p.kernel, st, &h->launches);
+    if (e == cudaErrorInvalidConfiguration) return fail(h, FRBX_EUNSUPPORTED, "fit kernel does not fit this shape");
+    FRBX_CK(h, e);
+  }
   FRBX_CK(h, cudaEventRecord(h->ev[3], st));
 
   // normalised power and threshold crossings of every baseline series

@@ -59,6 +59,29 @@ cudaError_t launch_fit(const FitArgs &a, int n_bl, bool list_mode, int kernel,
                        cudaStream_t st, int64_t *launches);
 bool fft_supported(int Ls, int Lm, int J);
 void set_fft_constants();
+// kernels_mma.cu: tensor-core (tcgen05, BF16) form of the MBD transform
+struct MmaArgs {
+  const void *bimg;        // constant operand B, already in its shared-memory image (BF16)
+  int b_bytes;             // bytes of the image
+  int b_atom_bytes;        // bytes of one 64-wide K atom of B (2 Lm rows x 128 B)
+  int KA;                  // K atoms (64 BF16 each) per row
+  int NC;                  // output columns per MMA chunk (Re G, Im G of NC/2 q values)
+  int n_chunk;             // 2 Lm / NC
+  int kk_steps;            // K / 16 MMA steps per chunk
+  int tmem_cols;           // tensor-memory columns allocated (2 accumulator slots)
+  int spt;                 // segments per 128-row tile (128 / Ls)
+  long long n_valid;       // segments to fit
+  long long per_bl;        // valid segments per baseline (implicit layout)
+  const long long *prefix; // [n_dm * n_win + 1] exclusive prefix of valid counts (implicit)
+  int n_prefix;
+  int *err;                // device flag, set to FRBX_ETIMEOUT when a bounded wait gives up
+  long long timeout;       // clock cycles per wait
+};
+bool mma_supported(int Ls, int Lm, int N, int J);
+void set_mma_constants();
+cudaError_t launch_fit_mma(const FitArgs &a, const MmaArgs &mm, int n_bl, bool list_mode, cudaStream_t st,
+                           int64_t *launches);
+
 // kernels_fft.cu
 cudaError_t launch_fit_fft(const FitArgs &a, int n_bl, bool list_mode, cudaStream_t st,
                            int64_t *launches);
@@ -127,11 +150,13 @@ struct frbx_handle {
   double *d_f = nullptr;
   float2 *d_wrot = nullptr, *d_tw_s = nullptr, *d_tw_m = nullptr;
   float2 *d_sbd_tw = nullptr, *d_mbd_tw = nullptr;
+  void *d_bimg = nullptr;  // BF16 DFT matrix image for the tensor-core fit (if supported)
+  int b_bytes = 0, b_atom_bytes = 0, KA = 0, NC = 0;
   int *d_g = nullptr, *d_slot = nullptr;
   // scratch, grown on demand
   struct Buf {
     void *p = nullptr;
     size_t bytes = 0;
   };
-  Buf vis, dk, dk_max, series, pnorm, stats, counts, offsets, events, small, seglist, masks;
+  Buf vis, dk, dk_max, series, pnorm, stats, counts, offsets, events, small, seglist, masks, prefix, errflag;
 };

@@ -1,0 +1,428 @@
+// Segment fit with the MBD transform as a BF16 DFT-GEMM on the tcgen05 tensor cores
+// (Eq. 3 gather and the SBD transform in FP32 on the CUDA cores, Eq. 5's sum over channels
+// as a dense GEMM with FP32 accumulation in tensor memory, grid maximum on the CUDA cores).
+//
+// For one M = 128 row tile (Ls = 128: one segment; Ls = 64: two), with K = 2N real inputs
+// per row (Re Y, Im Y of every channel) and the output columns split in chunks of NC:
+//     D[m][c] = sum_k A[m][k] B[c][k],  A[m][n] = Re Y(n, m), A[m][N + n] = Im Y(n, m),
+//     B rows of a chunk: first NC/2 give Re G(m, q), the next NC/2 give Im G(m, q) with
+//     Re G = sum_n Re Y cos th + Im Y sin th,  Im G = sum_n Im Y cos th - Re Y sin th,
+//     th = 2 pi (g_n q mod Lm) / Lm  (the phase index is exact; only cos/sin are rounded).
+//
+// Roles (288 threads):  warps 0-3 gather + SBD FFT -> A tile (BF16, 128B-swizzled, K-major);
+// warp 8 allocates tensor memory and one lane issues tcgen05.mma per chunk into one of two
+// accumulator slots; warps 4-7 read the slot back with tcgen05.ld (warp w reads lanes
+// 32 (w % 4) ..), form |G|^2 and keep the maximum.  Hand-offs use mbarriers; every wait is
+// bounded by a clock limit after which the kernel records FRBX_ETIMEOUT, drains, frees its
+// tensor memory and returns.
+#include <cuda_bf16.h>
+
+#include "fft32.cuh"
+#include "fit_common.cuh"
+
+namespace frbx {
+
+namespace {
+
+constexpr int kProdWarps = 4, kEpiWarps = 4;
+constexpr int kMmaWarp = kProdWarps + kEpiWarps;
+constexpr int kMmaThreads = (kProdWarps + kEpiWarps + 1) * 32;
+constexpr int kRows = 128;          // M of one MMA tile
+constexpr int kAtomBytes = kRows * 128;  // one 64-wide K atom of an A tile (16 KB)
+
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(su32(b)) : "memory");
+}
+// Bounded wait for the completion of the phase with the given parity.  Returns false on
+// timeout or when another role raised the abort flag.
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile int *abort_flag,
+                                          long long limit) {
+  const long long t0 = clock64();
+  const uint32_t addr = su32(b);
+  for (;;) {
+    uint32_t ok;
+    asm volatile("{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.b32 %0, 1, 0, P;\n}\n"
+                 : "=r"(ok) : "r"(addr), "r"(parity) : "memory");
+    if (ok) return true;
+    if (abort_flag && *abort_flag) return false;
+    if (clock64() - t0 > limit) return false;
+  }
+}
+
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// byte offset of bf16 element (row, k) in a 128-row tile of 64-wide K atoms, 128B swizzle
+__device__ __forceinline__ uint32_t a_offset(int row, int k) {
+  return (uint32_t)((k >> 6) * kAtomBytes + (row >> 3) * 1024 + (row & 7) * 128 +
+                    ((((k & 63) >> 3) ^ (row & 7)) << 4) + (k & 7) * 2);
+}
+
+__device__ __forceinline__ void named_sync(int id, int n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+struct MmaLayout {
+  size_t b_off, a_off, x_off, stw_off, bytes;
+  int xs, ts;
+};
+
+__host__ __device__ inline MmaLayout mma_layout(const MmaArgs &m, int N, int Ls, int J1) {
+  MmaLayout l;
+  l.b_off = 0;
+  l.a_off = (size_t)m.b_bytes;
+  l.x_off = l.a_off + 2 * (size_t)m.KA * kAtomBytes;
+  l.xs = J1 * 32 + 1;
+  l.ts = J1 * 32 + 1;
+  l.stw_off = l.x_off + sizeof(float2) * (size_t)N * l.xs;
+  l.bytes = l.stw_off + sizeof(float2) * (size_t)(Ls / 32) * l.ts + 1024;  // +1024: base alignment
+  return l;
+}
+
+// (bl, d, l, k0) and output index of valid segment v.
+__device__ __forceinline__ void decode_segment(const FitArgs &a, const MmaArgs &m, long long v, int list,
+                                               int &bl, int &d, int &l, int &k0, long long &out) {
+  if (list) {
+    const int4 row = reinterpret_cast<const int4 *>(a.seg)[v];
+    bl = row.x;
+    d = row.y;
+    l = row.z;
+    k0 = row.w;
+    out = v;
+    return;
+  }
+  bl = (int)(v / m.per_bl);
+  const long long r = v - (long long)bl * m.per_bl;
+  int lo = 0, hi = m.n_prefix - 1;  // prefix[lo] <= r < prefix[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (m.prefix[mid] <= r) lo = mid; else hi = mid;
+  }
+  d = lo / a.n_win;
+  const int w = lo - d * a.n_win;
+  const int s = (int)(r - m.prefix[lo]);
+  l = a.win_len[w];
+  k0 = s * max(1, l / 2);
+  out = ((long long)bl * a.n_dm + d) * a.S_tot + a.win_off[w] + s;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kMmaThreads, 1)
+    k_fit_mma(const __grid_constant__ FitArgs a, const __grid_constant__ MmaArgs mm, int list) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ uint64_t bar_afull[2], bar_aempty[2], bar_accfull[2], bar_accempty[2], bar_drain;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  __shared__ float red_p[kEpiWarps];
+  __shared__ int red_i[kEpiWarps];
+
+  const int N = a.N, Ls = a.Ls, Lm = a.Lm;
+  const int PS = Ls >> 5, lps = __ffs(PS) - 1;
+  const MmaLayout L = mma_layout(mm, N, Ls, a.J1);
+  unsigned char *sB = smem + L.b_off;
+  unsigned char *sA = smem + L.a_off;
+  float2 *X = reinterpret_cast<float2 *>(smem + L.x_off);
+  float2 *stw = reinterpret_cast<float2 *>(smem + L.stw_off);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int JP = a.J1 * 32;
+  const int SPT = mm.spt;
+  const long long n_tiles = (mm.n_valid + SPT - 1) / SPT;
+
+  // ---- set-up: constant operand B, SBD twiddles, zeroed A tiles and X, barriers, TMEM
+  {
+    const uint4 *src = reinterpret_cast<const uint4 *>(mm.bimg);
+    uint4 *dst = reinterpret_cast<uint4 *>(sB);
+    for (int i = tid; i < mm.b_bytes / 16; i += blockDim.x) dst[i] = src[i];
+    uint4 *za = reinterpret_cast<uint4 *>(sA);
+    for (int i = tid; i < 2 * mm.KA * kAtomBytes / 16; i += blockDim.x) za[i] = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < N * L.xs; i += blockDim.x) X[i] = make_float2(0.f, 0.f);
+    for (int i = tid; i < PS * JP; i += blockDim.x) {
+      const int r = i / JP, c = i - r * JP;
+      stw[r * L.ts + c] = a.sbd_tw[i];
+    }
+  }
+  if (tid == 0) {
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&bar_afull[i], kProdWarps * 32);
+      mbar_init(&bar_aempty[i], 1);
+      mbar_init(&bar_accfull[i], 1);
+      mbar_init(&bar_accempty[i], kEpiWarps * 32);
+    }
+    mbar_init(&bar_drain, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == kMmaWarp) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_base)),
+                 "r"(mm.tmem_cols) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  volatile int *abortp = &abort_flag;
+
+  if (warp < kProdWarps) {
+    // ================= producers: gather (Eq. 3) + SBD FFT -> BF16 A tile =================
+    const int ptid = tid;  // 0..127
+    long long it = 0;
+    for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
+      const int b = (int)(it & 1);
+      const uint32_t use = (uint32_t)(it >> 1);
+      if (!mbar_wait(&bar_aempty[b], (use & 1) ^ 1, abortp, mm.timeout)) {
+        *abortp = 1;
+        break;
+      }
+      unsigned char *At = sA + (size_t)b * mm.KA * kAtomBytes;
+      for (int sl = 0; sl < SPT; ++sl) {
+        const long long v = tile * SPT + sl;
+        if (v >= mm.n_valid) break;
+        int bl, d, l, k0;
+        long long out;
+        decode_segment(a, mm, v, list, bl, d, l, k0, out);
+        // gather
+        const int *dk = a.dk + (size_t)d * a.C;
+        const size_t base = (size_t)bl * a.T + k0;
+        for (int c = ptid; c < a.C; c += kProdWarps * 32) {
+          const float2 *p = a.vis + (base + __ldg(dk + c)) * a.C + c;
+          float2 acc = make_float2(0.f, 0.f);
+#pragma unroll 4
+          for (int i = 0; i < l; ++i) {
+            const float2 vv = __ldg(p + (size_t)i * a.C);
+            acc.x += vv.x;
+            acc.y += vv.y;
+          }
+          const int n = c / a.J, j = c - n * a.J;
+          X[n * L.xs + j] = cmul(acc, __ldg(a.wrot + c));
+        }
+        named_sync(1, kProdWarps * 32);
+        // SBD four-step FFT, task (n, m1); rows sl * Ls + m of the A tile
+        for (int t = ptid; t < N * PS; t += kProdWarps * 32) {
+          const int n = t >> lps, m1 = t & (PS - 1);
+          float2 A[32];
+#pragma unroll
+          for (int k = 0; k < 32; ++k) A[k] = make_float2(0.f, 0.f);
+          const float2 *xr = X + n * L.xs;
+          const float2 *wr = stw + m1 * L.ts;
+          for (int j1 = 0; j1 < a.J1; ++j1) {
+#pragma unroll
+            for (int j2 = 0; j2 < 32; ++j2) A[j2] = cfma(A[j2], xr[j1 * 32 + j2], wr[j1 * 32 + j2]);
+          }
+          fft32_dif(A);
+#pragma unroll
+          for (int k = 0; k < 32; ++k) {
+            const int row = sl * Ls + m1 + PS * bitrev5(k);
+            *reinterpret_cast<__nv_bfloat16 *>(At + a_offset(row, n)) = __float2bfloat16_rn(A[k].x);
+            *reinterpret_cast<__nv_bfloat16 *>(At + a_offset(row, N + n)) = __float2bfloat16_rn(A[k].y);
+          }
+        }
+        named_sync(1, kProdWarps * 32);  // X is reused by the next segment
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(&bar_afull[b]);
+    }
+  } else if (warp == kMmaWarp) {
+    // ================= MMA issuer =================
+    long long it = 0, chunk_ctr = 0;
+    bool ok = true;
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(mm.NC >> 3) << 17) |
+                           ((uint32_t)(kRows >> 4) << 24);
+    for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++it) {
+      const int b = (int)(it & 1);
+      const uint32_t use = (uint32_t)(it >> 1);
+      if (!mbar_wait(&bar_afull[b], use & 1, abortp, mm.timeout)) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a_base = su32(sA + (size_t)b * mm.KA * kAtomBytes);
+      for (int c = 0; c < mm.n_chunk; ++c, ++chunk_ctr) {
+        const int s = (int)(chunk_ctr & 1);
+        const uint32_t su = (uint32_t)(chunk_ctr >> 1);
+        if (!mbar_wait(&bar_accempty[s], (su & 1) ^ 1, abortp, mm.timeout)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (lane == 0) {
+          const uint32_t d_tmem = tmem + (uint32_t)(s * mm.NC);
+          for (int kk = 0; kk < mm.kk_steps; ++kk) {
+            const uint32_t koff = (uint32_t)((kk >> 2) * kAtomBytes + (kk & 3) * 32);
+            const uint64_t ad = desc_sw128(a_base + koff);
+            const uint64_t bd = desc_sw128(su32(sB) + (uint32_t)((kk >> 2) * mm.b_atom_bytes) +
+                                           (uint32_t)(c * mm.NC * 128) + (uint32_t)((kk & 3) * 32));
+            const uint32_t accum = kk > 0 ? 1u : 0u;
+            asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                         ::"r"(d_tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(accum) : "memory");
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                       ::"r"(su32(&bar_accfull[s])) : "memory");
+        }
+        __syncwarp();
+      }
+      if (!ok) break;
+      if (lane == 0)
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     ::"r"(su32(&bar_aempty[b])) : "memory");
+      __syncwarp();
+    }
+    if (!ok) *abortp = 1;
+    // drain: a last commit lands only when every MMA this thread issued has completed,
+    // so tensor memory is never freed under an MMA in flight (bounded, ignores the abort flag)
+    if (lane == 0)
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                   ::"r"(su32(&bar_drain)) : "memory");
+    __syncwarp();
+    if (!mbar_wait(&bar_drain, 0, nullptr, mm.timeout)) *abortp = 1;
+  } else {
+    // ================= epilogue: |G|^2 and the grid maximum =================
+    const int ew = warp - kProdWarps;          // 0..3 == warp % 4: TMEM lane quarter
+    const int row = ew * 32 + lane;            // tile row
+    const int sl = row / Ls, m = row - sl * Ls;
+    const int half = mm.NC >> 1;
+    long long chunk_ctr = 0;
+    bool ok = true;
+    for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x) {
+      float bp = -1.f;
+      int bq = 0;
+      for (int c = 0; c < mm.n_chunk; ++c, ++chunk_ctr) {
+        const int s = (int)(chunk_ctr & 1);
+        const uint32_t su = (uint32_t)(chunk_ctr >> 1);
+        if (!mbar_wait(&bar_accfull[s], su & 1, abortp, mm.timeout)) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t t_row = tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(s * mm.NC);
+        for (int p0 = 0; p0 < half; p0 += 16) {
+          uint32_t re[16], im[16];
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                       : "=r"(re[0]), "=r"(re[1]), "=r"(re[2]), "=r"(re[3]), "=r"(re[4]), "=r"(re[5]), "=r"(re[6]),
+                         "=r"(re[7]), "=r"(re[8]), "=r"(re[9]), "=r"(re[10]), "=r"(re[11]), "=r"(re[12]), "=r"(re[13]),
+                         "=r"(re[14]), "=r"(re[15])
+                       : "r"(t_row + (uint32_t)p0));
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                       : "=r"(im[0]), "=r"(im[1]), "=r"(im[2]), "=r"(im[3]), "=r"(im[4]), "=r"(im[5]), "=r"(im[6]),
+                         "=r"(im[7]), "=r"(im[8]), "=r"(im[9]), "=r"(im[10]), "=r"(im[11]), "=r"(im[12]), "=r"(im[13]),
+                         "=r"(im[14]), "=r"(im[15])
+                       : "r"(t_row + (uint32_t)(half + p0)));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          unsigned key = 0u;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const float gr = __uint_as_float(re[j]), gi = __uint_as_float(im[j]);
+            const float pw = fmaf(gr, gr, gi * gi);
+            key = max(key, (__float_as_uint(pw) & ~31u) | (unsigned)(16 - j));
+          }
+          const int q = c * half + p0 + 16 - (int)(key & 31u);
+          const float pk = __uint_as_float(key & ~31u);
+          if (pk > bp || (pk == bp && q < bq)) {
+            bp = pk;
+            bq = q;
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mbar_arrive(&bar_accempty[s]);
+      }
+      if (!ok) break;
+      // reduce over the rows of each segment of the tile
+      float rp = bp;
+      int ri = m * Lm + bq;
+#pragma unroll
+      for (int off = 16; off; off >>= 1) {
+        const float p2 = __shfl_xor_sync(0xffffffffu, rp, off);
+        const int i2 = __shfl_xor_sync(0xffffffffu, ri, off);
+        better(rp, ri, p2, i2);
+      }
+      if (lane == 0) {
+        red_p[ew] = rp;
+        red_i[ew] = ri;
+      }
+      named_sync(2, kEpiWarps * 32);
+      const int wps = Ls / 32;  // epilogue warps per segment
+      if (lane == 0 && (ew % wps) == 0) {
+        float fp = red_p[ew];
+        int fi = red_i[ew];
+        for (int k = 1; k < wps; ++k) better(fp, fi, red_p[ew + k], red_i[ew + k]);
+        const long long v = tile * SPT + sl;
+        if (v < mm.n_valid) {
+          int bl, d, l, k0;
+          long long out;
+          decode_segment(a, mm, v, list, bl, d, l, k0, out);
+          frbx_seg r;
+          r.amp = sqrtf(fp);
+          r.sbd_idx = (uint16_t)(fi >> a.log2Lm);
+          r.mbd_idx = (uint16_t)(fi & (Lm - 1));
+          a.out[out] = r;
+        }
+      }
+      named_sync(2, kEpiWarps * 32);
+    }
+    if (!ok) *abortp = 1;
+  }
+
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == kMmaWarp)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(mm.tmem_cols) : "memory");
+  if (tid == 0 && abort_flag) atomicExch(mm.err, FRBX_ETIMEOUT);
+}
+
+__global__ void k_fill_invalid(frbx_seg *out, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    frbx_seg r;
+    r.amp = -1.f;
+    r.sbd_idx = 0;
+    r.mbd_idx = 0;
+    out[i] = r;
+  }
+}
+
+void set_mma_constants() { upload_w32(); }
+
+bool mma_supported(int Ls, int Lm, int N, int J) {
+  const int KA = (2 * N + 63) / 64;
+  const size_t b_bytes = (size_t)KA * 2 * Lm * 128;
+  return (Ls == 64 || Ls == 128) && J <= Ls && 2 * Lm >= 32 && (2 * Lm) % 32 == 0 && KA <= 2 &&
+         b_bytes <= 144 * 1024;
+}
+
+cudaError_t launch_fit_mma(const FitArgs &a, const MmaArgs &mm, int n_bl, bool list_mode, cudaStream_t st,
+                           int64_t *launches) {
+  (void)n_bl;
+  if (!mma_supported(a.Ls, a.Lm, a.N, a.J)) return cudaErrorInvalidConfiguration;
+  const MmaLayout L = mma_layout(mm, a.N, a.Ls, a.J1);
+  if (L.bytes > max_smem_optin()) return cudaErrorInvalidConfiguration;
+  if (!list_mode) {
+    const long long n = (long long)n_bl * a.n_dm * a.S_tot;
+    if (n > 0) {
+      k_fill_invalid<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a.out, n);
+      ++*launches;
+    }
+  }
+  if (mm.n_valid == 0) return cudaGetLastError();
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long n_tiles = (mm.n_valid + mm.spt - 1) / mm.spt;
+  const unsigned grid = (unsigned)(n_tiles < sms ? n_tiles : sms);
+  cudaError_t e = cudaFuncSetAttribute(k_fit_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
+  if (e != cudaSuccess) return e;
+  k_fit_mma<<<grid, kMmaThreads, L.bytes, st>>>(a, mm, list_mode ? 1 : 0);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+}  // namespace frbx
