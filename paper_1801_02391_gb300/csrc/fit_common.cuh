@@ -37,9 +37,36 @@ struct Seg {
   bool valid;
 };
 
-// Segment number i of this CTA's tile.  Implicit layout: blockIdx = (slot tile, d, bl).
-__device__ __forceinline__ bool tile_segment(const FitArgs &a, bool list, int i, const int *win_off,
-                                             const int *win_len, const int *nval, Seg &s) {
+// Window ranges of the time tile a CTA fits in the implicit layout (blockIdx = (DM trial, time
+// tile of TT APs, baseline)): window w contributes the slots s in [s_lo, s_lo + cnt) whose start
+// k0 = s * step(l) falls in the tile; slots at or beyond the DM's valid count are written as
+// empty.  DM trials vary fastest across the grid, so the CTAs resident at one time read the
+// same stretch of the cube (plus its dispersion halo) from L2.
+struct TileWin {
+  int s_lo[kMaxWin], cum[kMaxWin + 1], len[kMaxWin], off[kMaxWin], nval[kMaxWin];
+};
+
+__device__ __forceinline__ void tile_windows(const FitArgs &a, TileWin &tw) {
+  if (threadIdx.x == 0) {
+    const int t0 = blockIdx.y * a.TT;
+    int c = 0;
+    for (int w = 0; w < a.n_win; ++w) {
+      const int l = a.win_len[w], step = max(1, l / 2);
+      const int ns = a.T >= l ? (a.T - l) / step + 1 : 0;
+      const int lo = (t0 + step - 1) / step, hi = min((t0 + a.TT + step - 1) / step, ns);
+      tw.s_lo[w] = lo;
+      tw.cum[w] = c;
+      c += max(0, hi - lo);
+      tw.len[w] = l;
+      tw.off[w] = a.win_off[w];
+      tw.nval[w] = a.n_valid[blockIdx.x * a.n_win + w];
+    }
+    tw.cum[a.n_win] = c;
+  }
+}
+
+// Segment number i of this CTA.  List mode: rows [blockIdx.x * tile, ...) of the list.
+__device__ __forceinline__ bool tile_segment(const FitArgs &a, bool list, int i, const TileWin &tw, Seg &s) {
   if (list) {
     const long long r = (long long)blockIdx.x * a.tile + i;
     if (i >= a.tile || r >= a.n_seg) return false;
@@ -52,17 +79,16 @@ __device__ __forceinline__ bool tile_segment(const FitArgs &a, bool list, int i,
     s.valid = true;
     return true;
   }
-  const int slot = blockIdx.x * a.tile + i;
-  if (i >= a.tile || slot >= a.S_tot) return false;
+  if (i >= tw.cum[a.n_win]) return false;
   int w = 0;
-  while (w + 1 < a.n_win && slot >= win_off[w + 1]) ++w;
-  const int sidx = slot - win_off[w];
+  while (i >= tw.cum[w + 1]) ++w;
+  const int sidx = tw.s_lo[w] + (i - tw.cum[w]);
   s.bl = blockIdx.z;
-  s.d = blockIdx.y;
-  s.l = win_len[w];
+  s.d = blockIdx.x;
+  s.l = tw.len[w];
   s.k0 = sidx * max(1, s.l / 2);
-  s.valid = sidx < nval[w];
-  s.out = ((long long)s.bl * a.n_dm + s.d) * a.S_tot + slot;
+  s.valid = sidx < tw.nval[w];
+  s.out = ((long long)s.bl * a.n_dm + s.d) * a.S_tot + tw.off[w] + sidx;
   return true;
 }
 

@@ -231,11 +231,14 @@ int frbx_create(const frbx_setup *s, frbx_handle **out) {
   // FFT-kernel tables
   std::vector<float2> sbd_tw, mbd_tw;
   std::vector<int> slot;
-  if (h->Ls % 32 == 0 && h->Lm % 32 == 0) {
-    const int PS = h->Ls / 32, PM = h->Lm / 32, JP = h->J1 * 32;
+  if (h->Ls % 32 == 0) {  // SBD four-step table (FFT and tensor-core fits)
+    const int PS = h->Ls / 32, JP = h->J1 * 32;
     sbd_tw.assign((size_t)PS * JP, make_float2(0.f, 0.f));
     for (int m1 = 0; m1 < PS; ++m1)
       for (int j = 0; j < J; ++j) sbd_tw[(size_t)m1 * JP + j] = tws[(size_t)(((long long)j * m1) % h->Ls)];
+  }
+  if (h->Ls % 32 == 0 && h->Lm % 32 == 0) {  // MBD four-step tables (FFT fit)
+    const int PM = h->Lm / 32;
     mbd_tw.resize((size_t)N * PM);
     for (int n = 0; n < N; ++n)
       for (int q1 = 0; q1 < PM; ++q1)
@@ -658,6 +661,7 @@ extern "C" int frbx_search(frbx_handle *h, const void *vis, int32_t vis_on_devic
   a.n_valid = d_tab + 3 * frbx::kMaxWin;
   a.S_tot = L.S_tot;
   a.tile = 64;
+  a.TT = 64;
   a.out = (frbx_seg *)h->series.p;
   FRBX_CK(h, cudaEventRecord(h->ev[2], st));
   if (p.kernel == 3) {

@@ -40,7 +40,8 @@ struct FitArgs {
   const int *win_off;      // [n_win] slot offset within a series
   const int *n_valid;      // [n_dm][n_win]
   int S_tot;
-  int tile;                // slots per CTA
+  int tile;                // list mode: rows per CTA
+  int TT;                  // implicit layout: APs per time tile (one CTA per DM, tile, baseline)
   // explicit list
   const int *seg;          // [n_seg][4]
   long long n_seg;

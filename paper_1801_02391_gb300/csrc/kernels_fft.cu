@@ -47,10 +47,7 @@ __global__ void __launch_bounds__(kFftThreads, 4) k_fit_fft(const __grid_constan
   float2 *Y = X + N * L.xs;                      // [N][ys]
   float2 *stw = Y + N * L.ys;                    // [PS][ts]
   float2 *mtw = stw + PS * L.ts;                 // [N][PM]
-  int *win_off = reinterpret_cast<int *>(mtw + N * PM);
-  int *win_len = win_off + kMaxWin;
-  int *nval = win_len + kMaxWin;
-  float *rp = reinterpret_cast<float *>(nval + kMaxWin);
+  float *rp = reinterpret_cast<float *>(mtw + N * PM);
   int *ri = reinterpret_cast<int *>(rp + 32);
 
   for (int i = threadIdx.x; i < N * L.xs; i += blockDim.x) X[i] = make_float2(0.f, 0.f);
@@ -59,18 +56,13 @@ __global__ void __launch_bounds__(kFftThreads, 4) k_fit_fft(const __grid_constan
     stw[r * L.ts + c] = a.sbd_tw[i];
   }
   for (int i = threadIdx.x; i < N * PM; i += blockDim.x) mtw[i] = a.mbd_tw[i];
-  if (!list) {
-    for (int i = threadIdx.x; i < a.n_win; i += blockDim.x) {
-      win_off[i] = a.win_off[i];
-      win_len[i] = a.win_len[i];
-      nval[i] = a.n_valid[blockIdx.y * a.n_win + i];
-    }
-  }
+  __shared__ TileWin tw;
+  if (!list) tile_windows(a, tw);
   __syncthreads();
 
   for (int it = 0;; ++it) {
     Seg s;
-    if (!tile_segment(a, list, it, win_off, win_len, nval, s)) break;
+    if (!tile_segment(a, list, it, tw, s)) break;
     if (!s.valid) {
       if (threadIdx.x == 0) write_fit(a, s, -1.f, 0);
       continue;

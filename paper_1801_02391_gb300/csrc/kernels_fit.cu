@@ -20,28 +20,20 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_direct(FitArgs a, int list)
   float2 *tws = Y + a.N * a.Ls;                  // [Ls]
   float2 *twm = tws + a.Ls;                      // [Lm]
   int *gsh = reinterpret_cast<int *>(twm + a.Lm);  // [N]
-  int *win_off = gsh + a.N;                      // [kMaxWin]
-  int *win_len = win_off + kMaxWin;              // [kMaxWin]
-  int *nval = win_len + kMaxWin;                 // [kMaxWin]
-  float *rp = reinterpret_cast<float *>(nval + kMaxWin);  // [32]
+  float *rp = reinterpret_cast<float *>(gsh + a.N);  // [32]
   int *ri = reinterpret_cast<int *>(rp + 32);    // [32]
 
   for (int i = threadIdx.x; i < a.Ls; i += blockDim.x) tws[i] = a.tw_s[i];
   for (int i = threadIdx.x; i < a.Lm; i += blockDim.x) twm[i] = a.tw_m[i];
   for (int i = threadIdx.x; i < a.N; i += blockDim.x) gsh[i] = a.g[i];
-  if (!list) {
-    for (int i = threadIdx.x; i < a.n_win; i += blockDim.x) {
-      win_off[i] = a.win_off[i];
-      win_len[i] = a.win_len[i];
-      nval[i] = a.n_valid[blockIdx.y * a.n_win + i];
-    }
-  }
+  __shared__ TileWin tw;
+  if (!list) tile_windows(a, tw);
   __syncthreads();
 
   const int Ls = a.Ls, Lm = a.Lm, J = a.J, N = a.N;
   for (int it = 0;; ++it) {
     Seg s;
-    if (!tile_segment(a, list, it, win_off, win_len, nval, s)) break;
+    if (!tile_segment(a, list, it, tw, s)) break;
     if (!s.valid) {
       if (threadIdx.x == 0) write_fit(a, s, -1.f, 0);
       continue;
@@ -97,8 +89,14 @@ bool fit_grid(const FitArgs &a, int n_bl, bool list_mode, dim3 *grid) {
     if (nb > 0x7fffffffLL) return false;
     *grid = dim3((unsigned)nb, 1, 1);
   } else {
-    if (a.n_dm > 65535 || n_bl > 65535) return false;
-    *grid = dim3((unsigned)((a.S_tot + a.tile - 1) / a.tile), (unsigned)a.n_dm, (unsigned)n_bl);
+    if (n_bl > 65535) return false;
+    if (a.S_tot == 0) {
+      *grid = dim3(0, 1, 1);
+      return true;
+    }
+    const long long n_tt = ((long long)a.T + a.TT - 1) / a.TT;
+    if (n_tt > 65535) return false;
+    *grid = dim3((unsigned)a.n_dm, (unsigned)n_tt, (unsigned)n_bl);
   }
   return true;
 }

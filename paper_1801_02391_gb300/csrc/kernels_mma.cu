@@ -68,6 +68,14 @@ __device__ __forceinline__ uint32_t a_offset(int row, int k) {
 __device__ __forceinline__ void named_sync(int id, int n) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
+// Named barrier that also returns the OR of a predicate over its n threads (a uniform
+// decision for the whole role).
+__device__ __forceinline__ bool named_sync_or(int id, int n, bool pred) {
+  uint32_t out;
+  asm volatile("{\n .reg .pred pi, po;\n setp.ne.u32 pi, %1, 0;\n bar.red.or.pred po, %2, %3, pi;\n selp.u32 %0, 1, 0, po;\n}\n"
+               : "=r"(out) : "r"((uint32_t)pred), "r"(id), "r"(n) : "memory");
+  return out != 0;
+}
 
 struct MmaLayout {
   size_t b_off, a_off, x_off, stw_off, bytes;
@@ -180,7 +188,8 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
     for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
       const int b = (int)(it & 1);
       const uint32_t use = (uint32_t)(it >> 1);
-      if (!mbar_wait(&bar_aempty[b], (use & 1) ^ 1, abortp, mm.timeout)) {
+      const bool got = mbar_wait(&bar_aempty[b], (use & 1) ^ 1, abortp, mm.timeout);
+      if (named_sync_or(1, kProdWarps * 32, !got)) {
         *abortp = 1;
         break;
       }
@@ -241,7 +250,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
     for (long long tile = blockIdx.x; tile < n_tiles && ok; tile += gridDim.x, ++it) {
       const int b = (int)(it & 1);
       const uint32_t use = (uint32_t)(it >> 1);
-      if (!mbar_wait(&bar_afull[b], use & 1, abortp, mm.timeout)) {
+      if (!__all_sync(0xffffffffu, mbar_wait(&bar_afull[b], use & 1, abortp, mm.timeout))) {
         ok = false;
         break;
       }
@@ -250,7 +259,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
       for (int c = 0; c < mm.n_chunk; ++c, ++chunk_ctr) {
         const int s = (int)(chunk_ctr & 1);
         const uint32_t su = (uint32_t)(chunk_ctr >> 1);
-        if (!mbar_wait(&bar_accempty[s], (su & 1) ^ 1, abortp, mm.timeout)) {
+        if (!__all_sync(0xffffffffu, mbar_wait(&bar_accempty[s], (su & 1) ^ 1, abortp, mm.timeout))) {
           ok = false;
           break;
         }
@@ -284,7 +293,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                    ::"r"(su32(&bar_drain)) : "memory");
     __syncwarp();
-    if (!mbar_wait(&bar_drain, 0, nullptr, mm.timeout)) *abortp = 1;
+    if (!__all_sync(0xffffffffu, mbar_wait(&bar_drain, 0, nullptr, mm.timeout))) *abortp = 1;
   } else {
     // ================= epilogue: |G|^2 and the grid maximum =================
     const int ew = warp - kProdWarps;          // 0..3 == warp % 4: TMEM lane quarter
@@ -299,10 +308,9 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
       for (int c = 0; c < mm.n_chunk; ++c, ++chunk_ctr) {
         const int s = (int)(chunk_ctr & 1);
         const uint32_t su = (uint32_t)(chunk_ctr >> 1);
-        if (!mbar_wait(&bar_accfull[s], su & 1, abortp, mm.timeout)) {
-          ok = false;
-          break;
-        }
+        if (ok && !mbar_wait(&bar_accfull[s], su & 1, abortp, mm.timeout)) ok = false;
+        if (!__all_sync(0xffffffffu, ok)) ok = false;  // tcgen05.ld below is warp-collective
+        if (!ok) continue;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t t_row = tmem + ((uint32_t)(ew * 32) << 16) + (uint32_t)(s * mm.NC);
         for (int p0 = 0; p0 < half; p0 += 16) {
@@ -335,7 +343,6 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         mbar_arrive(&bar_accempty[s]);
       }
-      if (!ok) break;
       // reduce over the rows of each segment of the tile
       float rp = bp;
       int ri = m * Lm + bq;
@@ -349,7 +356,10 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
         red_p[ew] = rp;
         red_i[ew] = ri;
       }
-      named_sync(2, kEpiWarps * 32);
+      if (named_sync_or(2, kEpiWarps * 32, !ok)) {
+        ok = false;
+        break;
+      }
       const int wps = Ls / 32;  // epilogue warps per segment
       if (lane == 0 && (ew % wps) == 0) {
         float fp = red_p[ew];

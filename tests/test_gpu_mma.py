@@ -1,0 +1,100 @@
+"""Tensor-core fit (kernel 3: MBD transform as a BF16 DFT-GEMM on tcgen05, FP32 accumulation)
+against the FP64 oracle.  BF16 operands carry 8 significant bits, so the amplitudes are
+compared with a stated error budget instead of the FP32 path's 1e-4:
+  * |G| at the reported cell: relative error <= 2e-2 per segment, median <= 4e-3;
+  * reported cell: its oracle |G| is within 3e-2 of the oracle maximum;
+  * detections: every oracle crossing with P >= 7 is also a crossing of the BF16 search.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import reference as R
+from paper_1801_02391_gb300 import _build
+from tests.test_gpu_parity import to_dev, valid_segments
+
+pytestmark = pytest.mark.gpu
+
+AMP_MAX_REL = 2e-2
+AMP_MEDIAN_REL = 4e-3
+CELL_REL = 3e-2
+
+
+@pytest.fixture(scope="module")
+def frbx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    _build.build()
+    from paper_1801_02391_gb300 import frbx as f
+    f.load()
+    return f
+
+
+def _check(st, vis, dk, segs, gpu):
+    a, m, q, a2, grid = R.fit_segments(st, vis, dk, segs, want_grid=True)
+    ga = gpu["amp"].astype(np.float64)
+    rel = np.abs(ga - a) / a
+    cell = np.abs(grid[np.arange(len(segs)), gpu["sbd_idx"].astype(int), gpu["mbd_idx"].astype(int)])
+    cell_rel = (a - cell) / a
+    print(f"bf16 amp rel err: max {rel.max():.2e} median {np.median(rel):.2e}; cell deficit max {cell_rel.max():.2e}; "
+          f"same cell {np.mean((gpu['sbd_idx'] == m) & (gpu['mbd_idx'] == q)):.3f}")
+    assert rel.max() <= AMP_MAX_REL and np.median(rel) <= AMP_MEDIAN_REL
+    assert cell_rel.max() <= CELL_REL
+    return rel
+
+
+@pytest.mark.parametrize("maker", ["vgos", "small"])
+def test_mma_fit_segments_vs_oracle(frbx, maker):
+    if maker == "vgos":
+        wl = synth.make_vgos(T=300, n_bl=2)
+        wl.dms = np.array([0.0, 40.0, 100.0, 150.0])
+    else:
+        wl = synth.make_small(T=700, dms=[0.0, 250.0, 557.0, 560.0])
+    st = R.setup_from_workload(wl)
+    vis = synth.generate(wl)
+    dk = R.shift_table(st, wl.dms)
+    segs = valid_segments(np.random.default_rng(21), wl, dk.max(axis=1), 301)
+    h = frbx.Handle.from_workload(wl)
+    gpu = h.fit_segments(to_dev(vis), wl.dms, segs, kernel=3)
+    _check(st, vis, dk, segs, gpu)
+    # the FP32 path on the same rows for reference
+    gpu32 = h.fit_segments(to_dev(vis), wl.dms, segs, kernel=1)
+    assert np.all(np.abs(gpu32["amp"] - gpu["amp"]) <= AMP_MAX_REL * gpu32["amp"])
+
+
+@pytest.mark.parametrize("maker", ["vgos", "small"])
+def test_mma_search_detections(frbx, maker):
+    """Whole search with kernel 3: series within the budget, strong crossings all found."""
+    if maker == "vgos":
+        wl = synth.make_vgos(T=1500, n_bl=2, n_dm=4)
+        wl.dms = np.array([0.0, 200.0, 400.0, 900.0])
+        for p in wl.pulses:
+            p.t0_bin = int(p.t0_bin % 200 + 50)
+            p.dm = 400.0
+    else:
+        wl = synth.make_small(T=4096, dms=np.arange(530.0, 591.0, 10.0))
+    st = R.setup_from_workload(wl)
+    vis = synth.generate(wl)
+    res = R.search(st, vis, wl.dms, wl.windows)
+    h = frbx.Handle.from_workload(wl)
+    out = h.search(to_dev(vis), wl.dms, wl.windows, kernel=3, want_series=True, want_events=True)
+    ser = out["series"]
+    valid = ~np.isnan(res.amp)
+    assert np.array_equal(ser["amp"] >= 0, valid)
+    rel = np.abs(ser["amp"][valid] - res.amp[valid]) / res.amp[valid]
+    print(f"search bf16 amp rel err: max {rel.max():.2e} median {np.median(rel):.2e}")
+    assert rel.max() <= AMP_MAX_REL and np.median(rel) <= AMP_MEDIAN_REL
+    g = {(int(e["series"]), int(e["dm_idx"]), int(e["win_idx"]), int(e["k0"])) for e in out["events"]}
+    strong = [(s, d, c.w, c.k0) for (s, d), lst in res.events.items() for c in lst if c.p >= 7.0]
+    assert strong and all(k in g for k in strong)
+
+
+def test_mma_rejects_delay_windows(frbx):
+    wl = synth.make_vgos(T=64, n_bl=1)
+    wl.dms = np.array([0.0])
+    h = frbx.Handle.from_workload(wl)
+    with pytest.raises(frbx.FrbxError) as e:
+        h.fit_segments(to_dev(synth.generate(wl)), wl.dms, np.array([[0, 0, 2, 0]], np.int32), kernel=3,
+                       sbd_win_ns=(-50.0, 50.0))
+    assert e.value.code == frbx.FRBX_EUNSUPPORTED
