@@ -299,6 +299,35 @@ int frbx_extract_events(const frbx_event *events, int64_t n_events, int32_t n_se
  */
 int frbx_last_stage_times(const frbx_handle *h, double *ms_out, int32_t n);
 
+/*
+ * Allocation-free segment fit.  The paper has no counterpart: this entry point exists for
+ * callers that must not allocate device memory at the point of the call -- for example a
+ * real-time back end that reserves all device memory at start-up, code running under a
+ * framework's caching allocator that must not see foreign cudaMalloc calls, or code that
+ * cannot afford the device-wide synchronisation cudaMalloc / cudaFree may imply.  It
+ * computes what frbx_fit_segments computes with the direct-DFT kernel (kernel 1), but
+ * needs no handle and calls no cudaMalloc, cudaFree or other allocating routine.
+ *
+ *  setup    observing setup as for frbx_create (read during the call only).
+ *  vis_dev  device cube [n_bl][T][n_chan*n_point] complex64, 8-byte aligned.
+ *  dm       host [n_dm] DM trials;  segs  host [n_seg][4] rows (bl, dm_idx, l, k0).
+ *  out_dev  device frbx_seg [n_seg], 8-byte aligned.
+ * Scratch: one fixed array of 16 MiB inside the library, in device memory of every GPU
+ * that loads it, held until the process exits.  A call needs, rounded up to 256 bytes per
+ * piece, about 4 n_dm n_chan n_point + 16 n_seg + 17 n_chan n_point + 8 (Ls + Lm) bytes;
+ * a call that would need more returns FRBX_EINVAL without running anything.
+ * The first call on a device looks the array up (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Every call on a device shares
+ * the array and it keeps the last call's contents: calls that overlap on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * Returns after the work on cuda_stream has finished.
+ * Errors: FRBX_EINVAL (bad argument, a row reading outside the cube, scratch too small),
+ * FRBX_EUNSUPPORTED, FRBX_ECUDA.
+ */
+int frbx_fit_segments_noalloc(const frbx_setup *setup, const void *vis_dev, int32_t n_bl, int32_t T,
+                              const double *dm, int32_t n_dm, const int32_t *segs, int64_t n_seg,
+                              frbx_seg *out_dev, void *cuda_stream);
+
 /* Number of kernel launches issued by the last frbx_search / frbx_fit_segments call. */
 int64_t frbx_last_launch_count(const frbx_handle *h);
 

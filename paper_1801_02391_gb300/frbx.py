@@ -104,6 +104,8 @@ SIGNATURES = {
                                   P(frbx_params), c_vp, c_vp]),
     "frbx_last_launch_count": (c_i64, [c_vp]),
     "frbx_last_stage_times": (c_i32, [c_vp, P(c_f64), c_i32]),
+    "frbx_fit_segments_noalloc": (c_i32, [P(frbx_setup), c_vp, c_i32, c_i32, P(c_f64), c_i32, P(c_i32), c_i64,
+                                          c_vp, c_vp]),
     "frbx_extract_events": (c_i32, [c_vp, c_i64, c_i32, c_i32, c_i32, P(c_i32), c_i32, c_i32, c_i32, c_i32,
                                     c_vp, c_i64, P(c_i64), c_vp, c_i64, P(c_i64), c_vp, c_i64, P(c_i64)]),
 }
