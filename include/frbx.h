@@ -328,6 +328,38 @@ int frbx_fit_segments_noalloc(const frbx_setup *setup, const void *vis_dev, int3
                               const double *dm, int32_t n_dm, const int32_t *segs, int64_t n_seg,
                               frbx_seg *out_dev, void *cuda_stream);
 
+/*
+ * Candidate refinement below the grid spacing (Eq. 4 with its delay-rate term kept; the fine
+ * DM search of Sec. 5.3).  For each candidate, the coherent power summed over baselines,
+ *   P = sum_b |G_b|^2,  G_b = sum_{n, j>=1} c(n,j) sum_{i<l} X_b(n, j, u(n,j) + i) exp(-i Phi),
+ *   u(n,j) = t0 + 4.15e6 DM (f^-2 - f_ref^-2) / t_ap   (continuous, no rounding),
+ *   X_b(.., x) = cubic Catmull-Rom interpolation of the cube along time at x,
+ *   Phi = 2 pi [(f_j tau_s + (f0_n - min f0) tau_m) 1e-3 + f0_n rho t_ap x 1e-6],
+ * with the argument of Phi and u in FP64 and the rest in FP32.
+ *  vis_dev    device cube [n_bl][T][n_chan*n_point] complex64.
+ *  params_dev device double [n_cand][2 + 3 n_bl]: DM (pc cm^-3), t0 (APs, window start at the
+ *             DM reference frequency), then per baseline tau_s (ns), tau_m (ns), rho (ns/s).
+ *  width_dev  device int32 [n_cand] window lengths l (APs, >= 1).
+ *  power_dev  device float [n_cand] out P;  g_dev device float [n_cand][n_bl][2] out G_b
+ *             (keep it for frbx_refine_adjoint).
+ *  status_dev device int32 [n_cand] out: 1 if some interpolation taps fell outside the cube
+ *             (those samples count as zero), else 0.
+ * Errors: FRBX_EINVAL, FRBX_ECUDA.
+ */
+int frbx_refine_power(frbx_handle *h, const void *vis_dev, int32_t n_bl, int32_t T, const double *params_dev,
+                      const int32_t *width_dev, int32_t n_cand, float *power_dev, float *g_dev,
+                      int32_t *status_dev, void *cuda_stream);
+
+/*
+ * Adjoint of frbx_refine_power: dparams[c][k] = dpower[c] * dP_c / dparams[c][k], from the G_b
+ * that frbx_refine_power returned for the same parameters.
+ *  dpower_dev  device float [n_cand] upstream gradient;  dparams_dev device float [n_cand][2 + 3 n_bl].
+ * Errors: FRBX_EINVAL, FRBX_ENOMEM, FRBX_ECUDA.
+ */
+int frbx_refine_adjoint(frbx_handle *h, const void *vis_dev, int32_t n_bl, int32_t T, const double *params_dev,
+                        const int32_t *width_dev, int32_t n_cand, const float *g_dev, const float *dpower_dev,
+                        float *dparams_dev, void *cuda_stream);
+
 /* Number of kernel launches issued by the last frbx_search / frbx_fit_segments call. */
 int64_t frbx_last_launch_count(const frbx_handle *h);
 

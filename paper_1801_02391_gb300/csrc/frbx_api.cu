@@ -290,6 +290,7 @@ int frbx_create(const frbx_setup *s, frbx_handle **out) {
   }
   cudaError_t e = cudaGetDevice(&h->device);
   if (e == cudaSuccess) e = upload(&h->d_f, h->f);
+  if (e == cudaSuccess) e = upload(&h->d_f0, h->f0);
   if (e == cudaSuccess) e = upload(&h->d_wrot, wrot);
   if (e == cudaSuccess) e = upload(&h->d_tw_s, tws);
   if (e == cudaSuccess) e = upload(&h->d_tw_m, twm);
@@ -314,14 +315,14 @@ int frbx_create(const frbx_setup *s, frbx_handle **out) {
 
 void frbx_destroy(frbx_handle *h) {
   if (!h) return;
-  void *ptrs[] = {h->d_f, h->d_wrot, h->d_tw_s, h->d_tw_m, h->d_g, h->d_sbd_tw, h->d_mbd_tw, h->d_slot, h->d_bimg};
+  void *ptrs[] = {h->d_f, h->d_f0, h->d_wrot, h->d_tw_s, h->d_tw_m, h->d_g, h->d_sbd_tw, h->d_mbd_tw, h->d_slot, h->d_bimg};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : h->ev)
     if (e) cudaEventDestroy(e);
   frbx_handle::Buf *bufs[] = {&h->vis, &h->dk, &h->dk_max, &h->series, &h->pnorm, &h->stats,
                               &h->counts, &h->offsets, &h->events, &h->small, &h->seglist, &h->masks,
-                              &h->prefix, &h->errflag};
+                              &h->errflag, &h->refine};
   for (auto *b : bufs)
     if (b->p) cudaFree(b->p);
   delete h;
@@ -464,9 +465,8 @@ void to_cand(const frbx_handle *h, const frbx::Pulse &p, const double *dm, const
   c->dm = dm[p.d];
 }
 
-// Tensor-core fit of n_valid segments (implicit layout when prefix is non-empty, else list).
-int run_fit_mma(frbx_handle *h, const FitArgs &a, int n_bl, bool list_mode, long long n_valid,
-                const std::vector<long long> &prefix, cudaStream_t st) {
+// Tensor-core fit of n_valid segments (implicit layout of the search, or the list in a).
+int run_fit_mma(frbx_handle *h, const FitArgs &a, int n_bl, bool list_mode, long long n_valid, cudaStream_t st) {
   frbx::MmaArgs mm{};
   mm.bimg = h->d_bimg;
   mm.b_bytes = h->b_bytes;
@@ -480,15 +480,8 @@ int run_fit_mma(frbx_handle *h, const FitArgs &a, int n_bl, bool list_mode, long
   mm.tmem_cols = cols;
   mm.spt = 128 / h->Ls;
   mm.n_valid = n_valid;
+  mm.n_items = list_mode ? 0 : (long long)n_bl * ((a.T + a.TT - 1) / a.TT) * a.n_dm;
   mm.timeout = 2000000000LL;
-  if (!list_mode) {
-    FRBX_CK(h, ensure(h->prefix, sizeof(long long) * prefix.size()));
-    FRBX_CK(h, cudaMemcpyAsync(h->prefix.p, prefix.data(), sizeof(long long) * prefix.size(),
-                               cudaMemcpyHostToDevice, st));
-    mm.prefix = (const long long *)h->prefix.p;
-    mm.n_prefix = (int)prefix.size();
-    mm.per_bl = prefix.back();
-  }
   FRBX_CK(h, ensure(h->errflag, sizeof(int)));
   FRBX_CK(h, cudaMemsetAsync(h->errflag.p, 0, sizeof(int), st));
   mm.err = (int *)h->errflag.p;
@@ -579,7 +572,7 @@ extern "C" int frbx_fit_segments(frbx_handle *h, const void *vis, int32_t vis_on
   a.tile = 16;
   a.out = (frbx_seg *)h->series.p;
   if (p.kernel == 3) {
-    rc = run_fit_mma(h, a, n_bl, true, n_seg, {}, st);
+    rc = run_fit_mma(h, a, n_bl, true, n_seg, st);
     if (rc) return rc;
   } else {
     cudaError_t e = frbx::launch_fit(a, n_bl, true, p.kernel, st, &h->launches);
@@ -665,10 +658,9 @@ extern "C" int frbx_search(frbx_handle *h, const void *vis, int32_t vis_on_devic
   a.out = (frbx_seg *)h->series.p;
   FRBX_CK(h, cudaEventRecord(h->ev[2], st));
   if (p.kernel == 3) {
-    std::vector<long long> prefix((size_t)n_dm * n_win + 1, 0);
-    for (size_t i = 0; i < L.n_valid.size(); ++i) prefix[i + 1] = prefix[i] + L.n_valid[i];
-    FRBX_CK(h, cudaEventRecord(h->ev[2], st));
-    rc = run_fit_mma(h, a, n_bl, false, prefix.back() * n_bl, prefix, st);
+    long long nv = 0;
+    for (int v : L.n_valid) nv += v;
+    rc = run_fit_mma(h, a, n_bl, false, nv * n_bl, st);
     if (rc) return rc;
   } else {
     cudaError_t e = frbx::launch_fit(a, n_bl, false, p.kernel, st, &h->launches);
@@ -854,4 +846,73 @@ extern "C" int frbx_last_stage_times(const frbx_handle *h, double *ms_out, int32
   const int k = std::min(n, 5);
   for (int i = 0; i < k; ++i) ms_out[i] = h->stage_ms[i];
   return k;
+}
+
+namespace {
+
+int refine_common(frbx_handle *h, const void *vis_dev, int32_t n_bl, int32_t T, const double *params_dev,
+                  const int32_t *width_dev, int32_t n_cand, frbx::RefineArgs *r) {
+  if (!vis_dev || !params_dev || !width_dev || n_cand < 0 || n_cand > 65535 * 256)
+    return fail(h, FRBX_EINVAL, "bad refinement arguments");
+  if (n_bl < 1 || n_bl > frbx::kMaxBl || n_bl > 65535 || T < 4) return fail(h, FRBX_EINVAL, "bad n_bl or T");
+  if (((uintptr_t)vis_dev & 7u) != 0) return fail(h, FRBX_EINVAL, "vis must be 8-byte aligned");
+  r->vis = (const float2 *)vis_dev;
+  r->T = T;
+  r->C = h->C;
+  r->J = h->J;
+  r->n_bl = n_bl;
+  r->n_cand = n_cand;
+  r->n_par = 2 + 3 * n_bl;
+  r->f = h->d_f;
+  r->f0 = h->d_f0;
+  r->wrot = h->d_wrot;
+  r->f0_min = *std::min_element(h->f0.begin(), h->f0.end());
+  r->inv_fref2 = 1.0 / (h->f_ref * h->f_ref);
+  r->f_bw = h->f_bw;
+  r->t_ap = h->t_ap;
+  r->params = params_dev;
+  r->width = width_dev;
+  return FRBX_OK;
+}
+
+}  // namespace
+
+extern "C" int frbx_refine_power(frbx_handle *h, const void *vis_dev, int32_t n_bl, int32_t T,
+                                 const double *params_dev, const int32_t *width_dev, int32_t n_cand,
+                                 float *power_dev, float *g_dev, int32_t *status_dev, void *cuda_stream) {
+  if (!h) return FRBX_EINVAL;
+  h->launches = 0;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  frbx::RefineArgs r{};
+  int rc = refine_common(h, vis_dev, n_bl, T, params_dev, width_dev, n_cand, &r);
+  if (rc) return rc;
+  if (n_cand > 0 && (!power_dev || !g_dev || !status_dev)) return fail(h, FRBX_EINVAL, "missing output");
+  r.g = g_dev;
+  r.power = power_dev;
+  r.status = status_dev;
+  if (n_cand > 0) FRBX_CK(h, cudaMemsetAsync(status_dev, 0, sizeof(int32_t) * (size_t)n_cand, st));
+  FRBX_CK(h, frbx::launch_refine(r, false, st, &h->launches));
+  FRBX_CK(h, cudaStreamSynchronize(st));
+  return FRBX_OK;
+}
+
+extern "C" int frbx_refine_adjoint(frbx_handle *h, const void *vis_dev, int32_t n_bl, int32_t T,
+                                   const double *params_dev, const int32_t *width_dev, int32_t n_cand,
+                                   const float *g_dev, const float *dpower_dev, float *dparams_dev,
+                                   void *cuda_stream) {
+  if (!h) return FRBX_EINVAL;
+  h->launches = 0;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  frbx::RefineArgs r{};
+  int rc = refine_common(h, vis_dev, n_bl, T, params_dev, width_dev, n_cand, &r);
+  if (rc) return rc;
+  if (n_cand > 0 && (!g_dev || !dpower_dev || !dparams_dev)) return fail(h, FRBX_EINVAL, "missing input or output");
+  FRBX_CK(h, ensure(h->refine, sizeof(float) * 2 * (size_t)n_cand * n_bl + 16));
+  r.g = const_cast<float *>(g_dev);
+  r.dpower = dpower_dev;
+  r.dparams = dparams_dev;
+  r.partial = (float *)h->refine.p;
+  FRBX_CK(h, frbx::launch_refine(r, true, st, &h->launches));
+  FRBX_CK(h, cudaStreamSynchronize(st));
+  return FRBX_OK;
 }

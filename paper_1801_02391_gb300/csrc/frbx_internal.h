@@ -72,9 +72,7 @@ struct MmaArgs {
   int tmem_cols;           // tensor-memory columns allocated (2 accumulator slots)
   int spt;                 // segments per 128-row tile (128 / Ls)
   long long n_valid;       // segments to fit
-  long long per_bl;        // valid segments per baseline (implicit layout)
-  const long long *prefix; // [n_dm * n_win + 1] exclusive prefix of valid counts (implicit)
-  int n_prefix;
+  long long n_items;       // implicit layout: n_bl * ceil(T / TT) * n_dm work items
   int *err;                // device flag, set to FRBX_ETIMEOUT when a bounded wait gives up
   long long timeout;       // clock cycles per wait
 };
@@ -82,6 +80,25 @@ bool mma_supported(int Ls, int Lm, int N, int J);
 void set_mma_constants();
 cudaError_t launch_fit_mma(const FitArgs &a, const MmaArgs &mm, int n_bl, bool list_mode, cudaStream_t st,
                            int64_t *launches);
+
+// kernels_refine.cu: coherent power of continuous (DM, t0, tau_s, tau_m, rho) and its adjoint
+struct RefineArgs {
+  const float2 *vis;       // [n_bl][T][C]
+  int T, C, J, n_bl, n_cand, n_par;
+  const double *f;         // [C] point frequencies
+  const double *f0;        // [N] channel edges
+  const float2 *wrot;      // [C]
+  double f0_min, inv_fref2, f_bw, t_ap;
+  const double *params;    // [n_cand][n_par]
+  const int *width;        // [n_cand]
+  float *g;                // [n_cand][n_bl][2]
+  float *power;            // [n_cand]
+  int *status;             // [n_cand]
+  const float *dpower;     // [n_cand]
+  float *dparams;          // [n_cand][n_par]
+  float *partial;          // [n_cand][n_bl][2] scratch
+};
+cudaError_t launch_refine(const RefineArgs &r, bool adjoint, cudaStream_t st, int64_t *launches);
 
 // kernels_fft.cu
 cudaError_t launch_fit_fft(const FitArgs &a, int n_bl, bool list_mode, cudaStream_t st,
@@ -148,7 +165,7 @@ struct frbx_handle {
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   double stage_ms[5] = {0, 0, 0, 0, 0};
   // constant device tables
-  double *d_f = nullptr;
+  double *d_f = nullptr, *d_f0 = nullptr;
   float2 *d_wrot = nullptr, *d_tw_s = nullptr, *d_tw_m = nullptr;
   float2 *d_sbd_tw = nullptr, *d_mbd_tw = nullptr;
   void *d_bimg = nullptr;  // BF16 DFT matrix image for the tensor-core fit (if supported)
@@ -159,5 +176,5 @@ struct frbx_handle {
     void *p = nullptr;
     size_t bytes = 0;
   };
-  Buf vis, dk, dk_max, series, pnorm, stats, counts, offsets, events, small, seglist, masks, prefix, errflag;
+  Buf vis, dk, dk_max, series, pnorm, stats, counts, offsets, events, small, seglist, masks, errflag, refine;
 };

@@ -104,6 +104,8 @@ SIGNATURES = {
                                   P(frbx_params), c_vp, c_vp]),
     "frbx_last_launch_count": (c_i64, [c_vp]),
     "frbx_last_stage_times": (c_i32, [c_vp, P(c_f64), c_i32]),
+    "frbx_refine_power": (c_i32, [c_vp, c_vp, c_i32, c_i32, c_vp, c_vp, c_i32, c_vp, c_vp, c_vp, c_vp]),
+    "frbx_refine_adjoint": (c_i32, [c_vp, c_vp, c_i32, c_i32, c_vp, c_vp, c_i32, c_vp, c_vp, c_vp, c_vp]),
     "frbx_fit_segments_noalloc": (c_i32, [P(frbx_setup), c_vp, c_i32, c_i32, P(c_f64), c_i32, P(c_i32), c_i64,
                                           c_vp, c_vp]),
     "frbx_extract_events": (c_i32, [c_vp, c_i64, c_i32, c_i32, c_i32, P(c_i32), c_i32, c_i32, c_i32, c_i32,
@@ -372,3 +374,56 @@ class Handle:
             out["series"] = ser_host.reshape(n_bl, len(dm), S_tot)
             out["pnorm"] = pn_host.reshape(n_bl, len(dm), S_tot)
         return out
+
+
+# ------------------------------------------------------------------ refinement (autograd)
+def _dp(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def refine_power(handle, vis_dev, params, width, stream=None):
+    """P [n_cand] (float32), G [n_cand][n_bl][2] and edge status for CUDA tensors
+    params (float64 [n_cand][2 + 3 n_bl]) and width (int32 [n_cand])."""
+    import torch
+    n_bl, T, _ = vis_dev.shape
+    n = params.shape[0]
+    power = torch.empty(n, dtype=torch.float32, device=params.device)
+    g = torch.empty((n, n_bl, 2), dtype=torch.float32, device=params.device)
+    status = torch.empty(n, dtype=torch.int32, device=params.device)
+    _check(handle.h, load().frbx_refine_power(handle.h, _dp(vis_dev), n_bl, T, _dp(params), _dp(width), n,
+                                              _dp(power), _dp(g), _dp(status), _stream_ptr(stream)))
+    return power, g, status
+
+
+def refine_adjoint(handle, vis_dev, params, width, g, dpower, stream=None):
+    import torch
+    n_bl, T, _ = vis_dev.shape
+    n = params.shape[0]
+    dparams = torch.empty((n, 2 + 3 * n_bl), dtype=torch.float32, device=params.device)
+    _check(handle.h, load().frbx_refine_adjoint(handle.h, _dp(vis_dev), n_bl, T, _dp(params), _dp(width), n,
+                                                _dp(g), _dp(dpower.contiguous()), _dp(dparams), _stream_ptr(stream)))
+    return dparams
+
+
+def coherent_power_fn():
+    """torch.autograd.Function whose forward is frbx_refine_power and whose backward is the
+    hand-written adjoint kernel frbx_refine_adjoint (argument marshalling only)."""
+    import torch
+
+    class CoherentPower(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, params, handle, vis_dev, width):
+            p = params.detach().contiguous()
+            power, g, status = refine_power(handle, vis_dev, p, width)
+            ctx.save_for_backward(p, g)
+            ctx.handle, ctx.vis, ctx.width = handle, vis_dev, width
+            ctx.status = status
+            return power
+
+        @staticmethod
+        def backward(ctx, dpower):
+            p, g = ctx.saved_tensors
+            dparams = refine_adjoint(ctx.handle, ctx.vis, p, ctx.width, g, dpower.float())
+            return dparams.to(p.dtype), None, None, None
+
+    return CoherentPower
