@@ -360,6 +360,20 @@ int frbx_refine_adjoint(frbx_handle *h, const void *vis_dev, int32_t n_bl, int32
                         const int32_t *width_dev, int32_t n_cand, const float *g_dev, const float *dpower_dev,
                         float *dparams_dev, void *cuda_stream);
 
+/*
+ * Initial phases and channel delays from a calibrator scan (Appendix A): the segment of APs
+ * [k0, k0 + l) at DM 0 is fringe-fitted on the grid (no calibration applied) for the common
+ * SBD and MBD; per channel, the delay maximising the channel power after removing the common
+ * SBD (grid of 8 J delays, parabolic start, Newton steps), then the residual phase.  The
+ * outputs plug into frbx_setup.chan_delay_ns / chan_phase_rad (Eq. 5) of a new handle.
+ *  vis, vis_on_device, n_bl, T  as in frbx_search.
+ *  sbd_ns, mbd_ns      host [n_bl] out;  delay_ns, phase_rad  host [n_bl][n_chan] out.
+ * Errors: FRBX_EINVAL, FRBX_ENOMEM, FRBX_ECUDA, FRBX_EUNSUPPORTED.
+ */
+int frbx_calibrate(frbx_handle *h, const void *vis, int32_t vis_on_device, int32_t n_bl, int32_t T, int32_t k0,
+                   int32_t l, double *sbd_ns, double *mbd_ns, double *delay_ns, double *phase_rad,
+                   void *cuda_stream);
+
 /* Number of kernel launches issued by the last frbx_search / frbx_fit_segments call. */
 int64_t frbx_last_launch_count(const frbx_handle *h);
 

@@ -322,7 +322,7 @@ void frbx_destroy(frbx_handle *h) {
     if (e) cudaEventDestroy(e);
   frbx_handle::Buf *bufs[] = {&h->vis, &h->dk, &h->dk_max, &h->series, &h->pnorm, &h->stats,
                               &h->counts, &h->offsets, &h->events, &h->small, &h->seglist, &h->masks,
-                              &h->errflag, &h->refine};
+                              &h->errflag, &h->refine, &h->calib};
   for (auto *b : bufs)
     if (b->p) cudaFree(b->p);
   delete h;
@@ -913,6 +913,80 @@ extern "C" int frbx_refine_adjoint(frbx_handle *h, const void *vis_dev, int32_t 
   r.dparams = dparams_dev;
   r.partial = (float *)h->refine.p;
   FRBX_CK(h, frbx::launch_refine(r, true, st, &h->launches));
+  FRBX_CK(h, cudaStreamSynchronize(st));
+  return FRBX_OK;
+}
+
+extern "C" int frbx_calibrate(frbx_handle *h, const void *vis, int32_t vis_on_device, int32_t n_bl, int32_t T,
+                              int32_t k0, int32_t l, double *sbd_ns, double *mbd_ns, double *delay_ns,
+                              double *phase_rad, void *cuda_stream) {
+  if (!h) return FRBX_EINVAL;
+  h->launches = 0;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (!sbd_ns || !mbd_ns || !delay_ns || !phase_rad) return fail(h, FRBX_EINVAL, "missing output");
+  if (k0 < 0 || l < 1 || (long long)k0 + l > T) return fail(h, FRBX_EINVAL, "calibrator segment outside the scan");
+  const float2 *dvis = nullptr;
+  int rc = check_vis(h, vis, vis_on_device, n_bl, T, st, &dvis);
+  if (rc) return rc;
+  const int C = h->C, N = h->N;
+  // scratch: FP64 sums, complex64 copy, unit weights, zero shifts, rows, fits, delays
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off = (off + bytes + 255) & ~(size_t)255;
+    return o;
+  };
+  const size_t o_xs = take(16 * (size_t)n_bl * C), o_xc = take(8 * (size_t)n_bl * C), o_w = take(8 * (size_t)C),
+               o_dk = take(4 * (size_t)C), o_rows = take(16 * (size_t)n_bl), o_fit = take(8 * (size_t)n_bl),
+               o_sm = take(16 * (size_t)n_bl), o_d = take(8 * (size_t)n_bl * N), o_p = take(8 * (size_t)n_bl * N);
+  FRBX_CK(h, ensure(h->calib, off));
+  unsigned char *b = (unsigned char *)h->calib.p;
+  FRBX_CK(h, frbx::launch_cal_sum(dvis, T, C, n_bl, k0, l, h->d_wrot, (double2 *)(b + o_xs), (float2 *)(b + o_xc),
+                                  (float2 *)(b + o_w), st, &h->launches));
+  FRBX_CK(h, cudaMemsetAsync(b + o_dk, 0, 4 * (size_t)C, st));
+  std::vector<int32_t> rows((size_t)4 * n_bl);
+  for (int i = 0; i < n_bl; ++i) {
+    rows[4 * i] = i;
+    rows[4 * i + 1] = 0;
+    rows[4 * i + 2] = 1;
+    rows[4 * i + 3] = 0;
+  }
+  FRBX_CK(h, cudaMemcpyAsync(b + o_rows, rows.data(), 16 * (size_t)n_bl, cudaMemcpyHostToDevice, st));
+  // (c) common fringe fit on the grid, no calibration rotation
+  FitArgs a{};
+  fill_fit_tables(h, &a, (const float2 *)(b + o_xc), 1, 1);
+  a.dk = (const int *)(b + o_dk);
+  a.wrot = (const float2 *)(b + o_w);
+  a.m_lo = 0;
+  a.m_len = h->Ls;
+  a.q_lo = 0;
+  a.q_len = h->Lm;
+  a.seg = (const int *)(b + o_rows);
+  a.n_seg = n_bl;
+  a.tile = 16;
+  a.out = (frbx_seg *)(b + o_fit);
+  cudaError_t e = frbx::launch_fit(a, n_bl, true, 0, st, &h->launches);
+  if (e == cudaErrorInvalidConfiguration) return fail(h, FRBX_EUNSUPPORTED, "fit kernel does not fit this shape");
+  FRBX_CK(h, e);
+  std::vector<frbx_seg> fits((size_t)n_bl);
+  FRBX_CK(h, cudaMemcpyAsync(fits.data(), b + o_fit, 8 * (size_t)n_bl, cudaMemcpyDeviceToHost, st));
+  FRBX_CK(h, cudaStreamSynchronize(st));
+  std::vector<double> sm((size_t)2 * n_bl);
+  for (int i = 0; i < n_bl; ++i) {
+    const int m = fits[(size_t)i].sbd_idx, q = fits[(size_t)i].mbd_idx;
+    const int sm_ = m < h->Ls / 2 ? m : m - h->Ls, sq = q < h->Lm / 2 ? q : q - h->Lm;
+    sm[(size_t)2 * i] = (((double)sm_ * h->J) * 1000.0) / ((double)h->Ls * h->f_bw);
+    sm[(size_t)2 * i + 1] = ((double)sq * 1000.0) / ((double)h->Lm * h->df_grid);
+    sbd_ns[i] = sm[(size_t)2 * i];
+    mbd_ns[i] = sm[(size_t)2 * i + 1];
+  }
+  FRBX_CK(h, cudaMemcpyAsync(b + o_sm, sm.data(), 16 * (size_t)n_bl, cudaMemcpyHostToDevice, st));
+  const double f0_min = *std::min_element(h->f0.begin(), h->f0.end());
+  FRBX_CK(h, frbx::launch_cal_channels((const double2 *)(b + o_xs), h->d_wrot, n_bl, N, h->J, h->f_bw, h->d_f0,
+                                       f0_min, (const double *)(b + o_sm), (double *)(b + o_d),
+                                       (double *)(b + o_p), st, &h->launches));
+  FRBX_CK(h, cudaMemcpyAsync(delay_ns, b + o_d, 8 * (size_t)n_bl * N, cudaMemcpyDeviceToHost, st));
+  FRBX_CK(h, cudaMemcpyAsync(phase_rad, b + o_p, 8 * (size_t)n_bl * N, cudaMemcpyDeviceToHost, st));
   FRBX_CK(h, cudaStreamSynchronize(st));
   return FRBX_OK;
 }

@@ -100,6 +100,13 @@ struct RefineArgs {
 };
 cudaError_t launch_refine(const RefineArgs &r, bool adjoint, cudaStream_t st, int64_t *launches);
 
+// kernels_calib.cu: Appendix A channel delays and initial phases
+cudaError_t launch_cal_sum(const float2 *vis, int T, int C, int n_bl, int k0, int l, const float2 *wrot,
+                           double2 *xsum, float2 *xcube, float2 *wunit, cudaStream_t st, int64_t *launches);
+cudaError_t launch_cal_channels(const double2 *xsum, const float2 *wrot, int n_bl, int N, int J, double f_bw,
+                                const double *f0, double f0_min, const double *sbd_mbd, double *delay_ns,
+                                double *phase_rad, cudaStream_t st, int64_t *launches);
+
 // kernels_fft.cu
 cudaError_t launch_fit_fft(const FitArgs &a, int n_bl, bool list_mode, cudaStream_t st,
                            int64_t *launches);
@@ -176,5 +183,5 @@ struct frbx_handle {
     void *p = nullptr;
     size_t bytes = 0;
   };
-  Buf vis, dk, dk_max, series, pnorm, stats, counts, offsets, events, small, seglist, masks, errflag, refine;
+  Buf vis, dk, dk_max, series, pnorm, stats, counts, offsets, events, small, seglist, masks, errflag, refine, calib;
 };

@@ -31,7 +31,7 @@ __host__ __device__ inline FftSmem fft_smem_layout(int N, int Ls, int Lm, int J1
   l.ts = JP + 1;
   l.bytes = sizeof(float2) * ((size_t)N * l.xs + (size_t)N * l.ys + (size_t)(Ls / 32) * l.ts +
                               (size_t)N * (Lm / 32)) +
-            sizeof(int) * (3 * kMaxWin) + 64 * sizeof(int);
+            16 * sizeof(int);  // block reduction (4 warps)
   return l;
 }
 
@@ -48,7 +48,7 @@ __global__ void __launch_bounds__(kFftThreads, 4) k_fit_fft(const __grid_constan
   float2 *stw = Y + N * L.ys;                    // [PS][ts]
   float2 *mtw = stw + PS * L.ts;                 // [N][PM]
   float *rp = reinterpret_cast<float *>(mtw + N * PM);
-  int *ri = reinterpret_cast<int *>(rp + 32);
+  int *ri = reinterpret_cast<int *>(rp + 8);
 
   for (int i = threadIdx.x; i < N * L.xs; i += blockDim.x) X[i] = make_float2(0.f, 0.f);
   for (int i = threadIdx.x; i < PS * JP; i += blockDim.x) {

@@ -106,6 +106,8 @@ SIGNATURES = {
     "frbx_last_stage_times": (c_i32, [c_vp, P(c_f64), c_i32]),
     "frbx_refine_power": (c_i32, [c_vp, c_vp, c_i32, c_i32, c_vp, c_vp, c_i32, c_vp, c_vp, c_vp, c_vp]),
     "frbx_refine_adjoint": (c_i32, [c_vp, c_vp, c_i32, c_i32, c_vp, c_vp, c_i32, c_vp, c_vp, c_vp, c_vp]),
+    "frbx_calibrate": (c_i32, [c_vp, c_vp, c_i32, c_i32, c_i32, c_i32, c_i32, P(c_f64), P(c_f64), P(c_f64),
+                               P(c_f64), c_vp]),
     "frbx_fit_segments_noalloc": (c_i32, [P(frbx_setup), c_vp, c_i32, c_i32, P(c_f64), c_i32, P(c_i32), c_i64,
                                           c_vp, c_vp]),
     "frbx_extract_events": (c_i32, [c_vp, c_i64, c_i32, c_i32, c_i32, P(c_i32), c_i32, c_i32, c_i32, c_i32,
@@ -300,6 +302,18 @@ class Handle:
         _check(self.h, load().frbx_shift_table(self.h, _ptr(dm, c_f64), len(dm), _ptr(out, c_i32),
                                                _stream_ptr(stream)))
         return out
+
+    def calibrate(self, vis, k0, l, stream=None):
+        """Appendix A: (sbd_ns [n_bl], mbd_ns [n_bl], delay_ns [n_bl][N], phase_rad [n_bl][N])."""
+        vp, on_dev, keep, shape = _vis_arg(vis)
+        n_bl, T, C = shape
+        sbd = np.zeros(n_bl)
+        mbd = np.zeros(n_bl)
+        dl = np.zeros((n_bl, self.n_chan))
+        ph = np.zeros((n_bl, self.n_chan))
+        _check(self.h, load().frbx_calibrate(self.h, vp, on_dev, n_bl, T, int(k0), int(l), _ptr(sbd, c_f64),
+                                             _ptr(mbd, c_f64), _ptr(dl, c_f64), _ptr(ph, c_f64), _stream_ptr(stream)))
+        return sbd, mbd, dl, ph
 
     def fit_segments(self, vis, dms, segs, kernel=0, sbd_win_ns=None, mbd_win_ns=None, stream=None):
         vp, on_dev, keep, shape = _vis_arg(vis)
