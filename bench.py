@@ -40,6 +40,17 @@ FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12  #
 # DRAM bytes per fitted segment of the fit kernel, from the ncu capture summarised in
 # profiles/fit_fft_vgos.md (None until a capture of the current kernel exists).
 FIT_DRAM_BYTES_PER_SEGMENT = None
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+
+
+def measured_peaks():
+    """HBM GB/s and BF16 TFLOP/s measured on this machine (MEASURED_PEAKS.json), else fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return {k: float(d[k]) for k in FALLBACK_PEAKS}, "measured"
+    except (OSError, KeyError, ValueError):
+        return dict(FALLBACK_PEAKS), "fallback"
 
 
 def parse():
@@ -53,6 +64,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel", type=int, default=0)
+    ap.add_argument("--no-variants", action="store_true", help="skip the tensor-core BF16 variant")
     return ap.parse_args()
 
 
@@ -92,6 +104,11 @@ def n_segments(wl, dk_max):
             if r >= 0:
                 tot += r // max(1, l // 2) + 1
     return tot * wl.n_bl
+
+
+def gemm_flops_per_segment(N, Ls, Lm):
+    """Dense DFT-GEMM form of the MBD transform: Ls rows x 2N real inputs x 2Lm real outputs."""
+    return 2.0 * Ls * (2 * N) * (2 * Lm)
 
 
 def fft_flops_per_segment(N, Ls, Lm):
@@ -298,6 +315,7 @@ def main():
             28 * (o["counts"]["events"] - o["counts"]["events_baseline"]) + 16 * (1 + len(combos))
     e2e = max_over_ranks(statistics.mean(e2e_ms))
 
+    peaks, peaks_kind = measured_peaks()
     flops = n_seg * fft_flops_per_segment(wl.n_chan, h.Ls, h.Lm)
     fit_mean = statistics.mean(fit_ms)
     achieved = flops / (fit_mean / 1e3) / 1e12
@@ -307,7 +325,8 @@ def main():
             "traffic": None if FIT_DRAM_BYTES_PER_SEGMENT is None else FIT_DRAM_BYTES_PER_SEGMENT * n_seg,
             "peak_note": "FP32 CUDA-core peak 152 SM x 128 lanes x 2 flop x 2070 MHz (derived, not measured)",
             "work": f"{n_seg} segments x {fft_flops_per_segment(wl.n_chan, h.Ls, h.Lm):.0f} flop (2-D FFT count)",
-            "fit_ms": fit_mean, "hbm_frac_8B_per_cell": (8.0 * cells / (ms / 1e3)) / 6687.5e9}
+            "fit_ms": fit_mean, "hbm_frac_8B_per_cell": (8.0 * cells / (ms / 1e3)) / (peaks["hbm_gbs"] * 1e9),
+            "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_kind": peaks_kind}
 
     line = {"metric": metric, "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -317,6 +336,41 @@ def main():
             "gpu_launches": launches, "roofline": roof, "clocks": clocks,
             "stages_ms": stages, "segments_per_step": n_seg,
             "pulses": int(out["counts"]["pulses"]), "groups": int(out["counts"]["groups"])}
+    # the tensor-core form (MBD transform as a BF16 DFT-GEMM on tcgen05), same workload
+    if not args.no_variants and args.kernel == 0 and h.Ls in (64, 128):
+        try:
+            for _ in range(1):
+                h.search(vis_dev, wl.dms, wl.windows, combos=combos, kernel=3, stream=stream)
+            barrier()
+            v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            vsteps = max(1, min(2, args.steps))
+            vfit = []
+            v0.record(stream)
+            for _ in range(vsteps):
+                o3 = h.search(vis_dev, wl.dms, wl.windows, combos=combos, kernel=3, stream=stream)
+                vfit.append(h.stage_times()["fit"])
+            v1.record(stream)
+            torch.cuda.synchronize()
+            vms = max_over_ranks(v0.elapsed_time(v1) / vsteps)
+            gflops = n_seg * gemm_flops_per_segment(wl.n_chan, h.Ls, h.Lm)
+            vach = gflops / (statistics.mean(vfit) / 1e3) / 1e12
+            line_variants = {"tensor_bf16": {
+                "value": world * cells / (vms / 1e3), "unit": "cells/s", "ms_per_step": vms, "steps": vsteps,
+                "dtype": "bf16 operands, f32 accumulate (MBD DFT-GEMM); f32 elsewhere",
+                "roofline": {"bound": "tensor", "kernel": "k_fit_mma", "achieved": vach,
+                             "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                             "frac": vach / peaks["bf16_tflops_sustained"], "traffic": None,
+                             "peak_kind": peaks_kind + " sustained bf16",
+                             "work": f"{n_seg} segments x {gemm_flops_per_segment(wl.n_chan, h.Ls, h.Lm):.0f} flop "
+                                     "(dense DFT-GEMM of the MBD transform)",
+                             "fit_ms": statistics.mean(vfit)},
+                "pulses": int(o3["counts"]["pulses"]), "groups": int(o3["counts"]["groups"])}}
+        except Exception as exc:  # a variant that cannot run on this setup is reported, not fatal
+            line_variants = {"tensor_bf16": {"unavailable": str(exc)}}
+    else:
+        line_variants = None
+    if line_variants:
+        line["variants"] = line_variants
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, desc, dt = run_oracle_sample(wl, vis_host[0], args.cpu_seconds)
         line["cpu_baseline"] = {"value": v, "unit": "cells/s", "cores": cores, "kind": "oracle", "sample": desc}

@@ -374,6 +374,52 @@ int frbx_calibrate(frbx_handle *h, const void *vis, int32_t vis_on_device, int32
                    int32_t l, double *sbd_ns, double *mbd_ns, double *delay_ns, double *phase_rad,
                    void *cuda_stream);
 
+/*
+ * Batched search: many scans, of uneven length and on several observing setups, in one pass.
+ * Every scan gets exactly what frbx_search would give it (same kernels, same arithmetic).
+ * The device work of the fit -- the dominant stage -- is one persistent launch per setup (and
+ * per distinct window layout), whose CTAs claim (scan, baseline, time tile, DM trial) work
+ * items from a device counter, so uneven scans load-balance; these launches are captured once
+ * into a CUDA graph and replayed while the scans' shapes and buffers stay the same.  The time
+ * tile of each setup is chosen by timing candidates (32, 64, 128 APs) on a sample of its
+ * items the first time a setup shape is seen by the batch object.
+ * Normalisation, threshold and extraction then run per scan as in frbx_search.
+ */
+typedef struct frbx_batch frbx_batch;
+
+typedef struct frbx_scan {
+  frbx_handle *setup;    /* handle of the scan's setup; scans may share one */
+  const void *vis_dev;   /* device cube [n_bl][T][n_chan*n_point] complex64, 8-byte aligned */
+  int32_t n_bl;
+  int32_t T;
+} frbx_scan;
+
+typedef struct frbx_batch_stats {
+  int32_t graph_captures;  /* times the fit graph was (re)captured by this batch object */
+  int32_t graph_replays;   /* times it was replayed without capture */
+  int32_t n_setups;        /* distinct setups in the last call */
+  int32_t time_tile[16];   /* chosen time tile (APs) per setup, in order of first appearance */
+  int32_t reserved;
+  double fit_ms;           /* device time of the last graph launch (all fits) */
+  int64_t launches;        /* kernel launches of the last call (graph kernels counted once) */
+} frbx_batch_stats;
+
+int frbx_batch_create(frbx_batch **out);
+void frbx_batch_destroy(frbx_batch *b);
+const char *frbx_batch_last_error(const frbx_batch *b);
+int frbx_batch_info(const frbx_batch *b, frbx_batch_stats *stats);
+
+/*
+ *  scans     [n_scans] (1..4096; at most 16 distinct setups).
+ *  dm, n_dm, windows, n_win, params  as in frbx_search, shared by all scans (kernel 0, 1 or 2;
+ *            combination masks must name baselines each scan has).
+ *  results   [n_scans] outputs, one frbx_results per scan (series outputs included).
+ * Errors: FRBX_EINVAL, FRBX_ENOMEM, FRBX_ECUDA, FRBX_ETRUNC, FRBX_EUNSUPPORTED.
+ */
+int frbx_search_batch(frbx_batch *b, const frbx_scan *scans, int32_t n_scans, const double *dm, int32_t n_dm,
+                      const int32_t *windows, int32_t n_win, const frbx_params *params, frbx_results *results,
+                      void *cuda_stream);
+
 /* Number of kernel launches issued by the last frbx_search / frbx_fit_segments call. */
 int64_t frbx_last_launch_count(const frbx_handle *h);
 

@@ -5,6 +5,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <numeric>
 #include <string>
@@ -522,6 +523,121 @@ int run_stats(frbx_handle *h, StatsArgs sa, cudaStream_t st, std::vector<frbx_ev
 
 }  // namespace
 
+// Everything after the fit (Eq. 6 and threshold on the device, then the host extraction of
+// Sec. 2.4.1 b-d, the DM merge of Sec. 5.3, cross-matching and the power sums of Sec. 2.4.2)
+// for one scan whose segment series are at `series`; d_tab holds the window tables and the
+// scan's valid-segment counts in the layout frbx_search uploads.
+int finish_search(frbx_handle *h, const frbx_seg *series, int n_bl, int T, const double *dm, int n_dm, int n_win,
+                  const Layout &L, const int *d_tab, const frbx_params &p, frbx_results *res, cudaStream_t st) {
+  int rc = FRBX_OK;
+  const size_t n_series_el = (size_t)n_bl * n_dm * L.S_tot;
+  // normalised power and threshold crossings of every baseline series
+  const bool want_p = res->pnorm && res->series_cap >= (int64_t)n_series_el;
+  float *pn = nullptr;
+  if (want_p) {
+    if (res->series_on_device) {
+      pn = res->pnorm;
+    } else {
+      FRBX_CK(h, ensure(h->pnorm, sizeof(float) * n_series_el));
+      pn = (float *)h->pnorm.p;
+    }
+    FRBX_CK(h, cudaMemsetAsync(pn, 0, sizeof(float) * n_series_el, st));
+  }
+  StatsArgs sa{};
+  sa.series = series;
+  sa.n_bl = n_bl;
+  sa.n_dm = n_dm;
+  sa.S_tot = L.S_tot;
+  sa.n_win = n_win;
+  sa.win_off = d_tab + frbx::kMaxWin;
+  sa.win_step = d_tab + 2 * frbx::kMaxWin;
+  sa.n_valid = d_tab + 3 * frbx::kMaxWin;
+  sa.threshold = (double)p.threshold;
+  sa.n_series = n_bl;
+  sa.masks = nullptr;
+  sa.pnorm = pn;
+  sa.series_base = 0;
+  std::vector<frbx_event> ev_bl, ev_cb;
+  rc = run_stats(h, sa, st, &ev_bl);
+  if (rc) return rc;
+  FRBX_CK(h, cudaEventRecord(h->ev[4], st));
+  if (p.n_combo > 0) {
+    FRBX_CK(h, ensure(h->masks, sizeof(uint64_t) * (size_t)p.n_combo));
+    FRBX_CK(h, cudaMemcpyAsync(h->masks.p, p.combos, sizeof(uint64_t) * p.n_combo, cudaMemcpyHostToDevice, st));
+    sa.masks = (const unsigned long long *)h->masks.p;
+    sa.n_series = p.n_combo;
+    sa.pnorm = nullptr;
+    rc = run_stats(h, sa, st, &ev_cb);
+    if (rc) return rc;
+  }
+  FRBX_CK(h, cudaEventRecord(h->ev[5], st));
+  FRBX_CK(h, cudaEventSynchronize(h->ev[5]));
+  {
+    float ms = 0.f;
+    const int pairs[4][2] = {{0, 1}, {2, 3}, {3, 4}, {4, 5}};
+    for (int k = 0; k < 4; ++k) {
+      FRBX_CK(h, cudaEventElapsedTime(&ms, h->ev[pairs[k][0]], h->ev[pairs[k][1]]));
+      h->stage_ms[k] = ms;
+    }
+  }
+  const auto host_t0 = std::chrono::steady_clock::now();
+
+  // host extraction (Sec. 2.4.1 b-d, Sec. 5.3 merge, cross-matching, Sec. 2.4.2)
+  frbx::ExtractConfig cfg{T, n_dm, n_win, p.nwin_min, h->Lm, L.win_len.data()};
+  std::vector<frbx::Pulse> pre, merged, comb;
+  std::vector<frbx::GroupOut> groups;
+  frbx::extract_pulses(cfg, ev_bl.data(), (int64_t)ev_bl.size(), n_bl, true, &pre, &merged);
+  frbx::cross_match(T, &merged, n_bl, &groups);
+  if (p.n_combo > 0)
+    frbx::extract_pulses(cfg, ev_cb.data(), (int64_t)ev_cb.size(), p.n_combo, false, nullptr, &comb);
+
+  h->stage_ms[4] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - host_t0).count();
+  bool trunc = false;
+  auto put_cands = [&](const std::vector<frbx::Pulse> &v, bool combined, frbx_cand *dst, int64_t cap,
+                       int64_t *count) {
+    *count = (int64_t)v.size();
+    if (cap > 0 && (int64_t)v.size() > cap) trunc = true;
+    if (!dst) return;
+    const int64_t n = std::min<int64_t>(cap, (int64_t)v.size());
+    for (int64_t i = 0; i < n; ++i) to_cand(h, v[(size_t)i], dm, L, combined, &dst[i]);
+  };
+  put_cands(merged, false, res->pulses, res->pulses_cap, &res->pulses_count);
+  put_cands(comb, true, res->combined, res->combined_cap, &res->combined_count);
+  put_cands(pre, false, res->pulses_dm, res->pulses_dm_cap, &res->pulses_dm_count);
+  res->groups_count = (int64_t)groups.size();
+  if (res->groups) {
+    const int64_t n = std::min<int64_t>(res->groups_cap, (int64_t)groups.size());
+    for (int64_t i = 0; i < n; ++i) {
+      res->groups[i].bl_mask = groups[(size_t)i].mask;
+      res->groups[i].n_baselines = groups[(size_t)i].n_baselines;
+      res->groups[i].n_pulses = groups[(size_t)i].n_pulses;
+    }
+  }
+  if (res->groups_cap > 0 && (int64_t)groups.size() > res->groups_cap) trunc = true;
+  res->events_count = (int64_t)(ev_bl.size() + ev_cb.size());
+  res->events_baseline_count = (int64_t)ev_bl.size();
+  if (res->events) {
+    int64_t k = 0;
+    for (const auto &ev : {&ev_bl, &ev_cb})
+      for (const frbx_event &x : *ev) {
+        if (k >= res->events_cap) break;
+        res->events[k++] = x;
+      }
+  }
+  if (res->events_cap > 0 && res->events_count > res->events_cap) trunc = true;
+  res->series_count = (int64_t)n_series_el;
+  if (res->series && res->series_cap >= (int64_t)n_series_el) {
+    FRBX_CK(h, cudaMemcpyAsync(res->series, series, sizeof(frbx_seg) * n_series_el,
+                               res->series_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  }
+  if (want_p && !res->series_on_device)
+    FRBX_CK(h, cudaMemcpyAsync(res->pnorm, pn, sizeof(float) * n_series_el, cudaMemcpyDeviceToHost, st));
+  if ((res->series || res->pnorm) && res->series_cap < (int64_t)n_series_el) trunc = true;
+  FRBX_CK(h, cudaStreamSynchronize(st));
+  if (trunc) return fail(h, FRBX_ETRUNC, "an output array was too small");
+  return FRBX_OK;
+}
+
 extern "C" int frbx_shift_table(frbx_handle *h, const double *dm, int32_t n_dm, int32_t *dk_out,
                                 void *cuda_stream) {
   if (!h) return FRBX_EINVAL;
@@ -669,111 +785,7 @@ extern "C" int frbx_search(frbx_handle *h, const void *vis, int32_t vis_on_devic
   }
   FRBX_CK(h, cudaEventRecord(h->ev[3], st));
 
-  // normalised power and threshold crossings of every baseline series
-  const bool want_p = res->pnorm && res->series_cap >= (int64_t)n_series_el;
-  float *pn = nullptr;
-  if (want_p) {
-    if (res->series_on_device) {
-      pn = res->pnorm;
-    } else {
-      FRBX_CK(h, ensure(h->pnorm, sizeof(float) * n_series_el));
-      pn = (float *)h->pnorm.p;
-    }
-    FRBX_CK(h, cudaMemsetAsync(pn, 0, sizeof(float) * n_series_el, st));
-  }
-  StatsArgs sa{};
-  sa.series = (const frbx_seg *)h->series.p;
-  sa.n_bl = n_bl;
-  sa.n_dm = n_dm;
-  sa.S_tot = L.S_tot;
-  sa.n_win = n_win;
-  sa.win_off = d_tab + frbx::kMaxWin;
-  sa.win_step = d_tab + 2 * frbx::kMaxWin;
-  sa.n_valid = d_tab + 3 * frbx::kMaxWin;
-  sa.threshold = (double)p.threshold;
-  sa.n_series = n_bl;
-  sa.masks = nullptr;
-  sa.pnorm = pn;
-  sa.series_base = 0;
-  std::vector<frbx_event> ev_bl, ev_cb;
-  rc = run_stats(h, sa, st, &ev_bl);
-  if (rc) return rc;
-  FRBX_CK(h, cudaEventRecord(h->ev[4], st));
-  if (p.n_combo > 0) {
-    FRBX_CK(h, ensure(h->masks, sizeof(uint64_t) * (size_t)p.n_combo));
-    FRBX_CK(h, cudaMemcpyAsync(h->masks.p, p.combos, sizeof(uint64_t) * p.n_combo, cudaMemcpyHostToDevice, st));
-    sa.masks = (const unsigned long long *)h->masks.p;
-    sa.n_series = p.n_combo;
-    sa.pnorm = nullptr;
-    rc = run_stats(h, sa, st, &ev_cb);
-    if (rc) return rc;
-  }
-  FRBX_CK(h, cudaEventRecord(h->ev[5], st));
-  FRBX_CK(h, cudaEventSynchronize(h->ev[5]));
-  {
-    float ms = 0.f;
-    const int pairs[4][2] = {{0, 1}, {2, 3}, {3, 4}, {4, 5}};
-    for (int k = 0; k < 4; ++k) {
-      FRBX_CK(h, cudaEventElapsedTime(&ms, h->ev[pairs[k][0]], h->ev[pairs[k][1]]));
-      h->stage_ms[k] = ms;
-    }
-  }
-  const auto host_t0 = std::chrono::steady_clock::now();
-
-  // host extraction (Sec. 2.4.1 b-d, Sec. 5.3 merge, cross-matching, Sec. 2.4.2)
-  frbx::ExtractConfig cfg{T, n_dm, n_win, p.nwin_min, h->Lm, L.win_len.data()};
-  std::vector<frbx::Pulse> pre, merged, comb;
-  std::vector<frbx::GroupOut> groups;
-  frbx::extract_pulses(cfg, ev_bl.data(), (int64_t)ev_bl.size(), n_bl, true, &pre, &merged);
-  frbx::cross_match(T, &merged, n_bl, &groups);
-  if (p.n_combo > 0)
-    frbx::extract_pulses(cfg, ev_cb.data(), (int64_t)ev_cb.size(), p.n_combo, false, nullptr, &comb);
-
-  h->stage_ms[4] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - host_t0).count();
-  bool trunc = false;
-  auto put_cands = [&](const std::vector<frbx::Pulse> &v, bool combined, frbx_cand *dst, int64_t cap,
-                       int64_t *count) {
-    *count = (int64_t)v.size();
-    if (cap > 0 && (int64_t)v.size() > cap) trunc = true;
-    if (!dst) return;
-    const int64_t n = std::min<int64_t>(cap, (int64_t)v.size());
-    for (int64_t i = 0; i < n; ++i) to_cand(h, v[(size_t)i], dm, L, combined, &dst[i]);
-  };
-  put_cands(merged, false, res->pulses, res->pulses_cap, &res->pulses_count);
-  put_cands(comb, true, res->combined, res->combined_cap, &res->combined_count);
-  put_cands(pre, false, res->pulses_dm, res->pulses_dm_cap, &res->pulses_dm_count);
-  res->groups_count = (int64_t)groups.size();
-  if (res->groups) {
-    const int64_t n = std::min<int64_t>(res->groups_cap, (int64_t)groups.size());
-    for (int64_t i = 0; i < n; ++i) {
-      res->groups[i].bl_mask = groups[(size_t)i].mask;
-      res->groups[i].n_baselines = groups[(size_t)i].n_baselines;
-      res->groups[i].n_pulses = groups[(size_t)i].n_pulses;
-    }
-  }
-  if (res->groups_cap > 0 && (int64_t)groups.size() > res->groups_cap) trunc = true;
-  res->events_count = (int64_t)(ev_bl.size() + ev_cb.size());
-  res->events_baseline_count = (int64_t)ev_bl.size();
-  if (res->events) {
-    int64_t k = 0;
-    for (const auto &ev : {&ev_bl, &ev_cb})
-      for (const frbx_event &x : *ev) {
-        if (k >= res->events_cap) break;
-        res->events[k++] = x;
-      }
-  }
-  if (res->events_cap > 0 && res->events_count > res->events_cap) trunc = true;
-  res->series_count = (int64_t)n_series_el;
-  if (res->series && res->series_cap >= (int64_t)n_series_el) {
-    FRBX_CK(h, cudaMemcpyAsync(res->series, h->series.p, sizeof(frbx_seg) * n_series_el,
-                               res->series_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
-  }
-  if (want_p && !res->series_on_device)
-    FRBX_CK(h, cudaMemcpyAsync(res->pnorm, pn, sizeof(float) * n_series_el, cudaMemcpyDeviceToHost, st));
-  if ((res->series || res->pnorm) && res->series_cap < (int64_t)n_series_el) trunc = true;
-  FRBX_CK(h, cudaStreamSynchronize(st));
-  if (trunc) return fail(h, FRBX_ETRUNC, "an output array was too small");
-  return FRBX_OK;
+  return finish_search(h, (const frbx_seg *)h->series.p, n_bl, T, dm, n_dm, n_win, L, d_tab, p, res, st);
 }
 
 extern "C" int frbx_extract_events(const frbx_event *events, int64_t n_events, int32_t n_series,
@@ -988,5 +1000,361 @@ extern "C" int frbx_calibrate(frbx_handle *h, const void *vis, int32_t vis_on_de
   FRBX_CK(h, cudaMemcpyAsync(delay_ns, b + o_d, 8 * (size_t)n_bl * N, cudaMemcpyDeviceToHost, st));
   FRBX_CK(h, cudaMemcpyAsync(phase_rad, b + o_p, 8 * (size_t)n_bl * N, cudaMemcpyDeviceToHost, st));
   FRBX_CK(h, cudaStreamSynchronize(st));
+  return FRBX_OK;
+}
+
+// ======================================================================================
+// Batched search over many scans (several setups, uneven lengths) with a persistent,
+// graph-captured fit and an autotuned time tile.
+// ======================================================================================
+struct frbx_batch {
+  std::string err;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::string key;
+  int captures = 0, replays = 0;
+  std::map<std::string, int> tuned_tt;  // setup shape + DM grid + windows -> time tile
+  frbx_handle::Buf desc, tables, series, counters;
+  std::vector<int> last_tt;
+  double last_fit_ms = 0.0;
+  int64_t launches = 0, graph_kernels = 0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaStream_t cap = nullptr;  // capture only (the legacy default stream cannot be captured)
+};
+
+namespace {
+
+int bfail(frbx_batch *b, int code, const std::string &msg) {
+  if (b) b->err = msg;
+  return code;
+}
+
+#define FRBX_BCK(b, call)                                                                  \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) {                                                               \
+      cudaGetLastError();                                                                  \
+      return bfail((b), e_ == cudaErrorMemoryAllocation ? FRBX_ENOMEM : FRBX_ECUDA,        \
+                   std::string(#call) + ": " + cudaGetErrorString(e_));                    \
+    }                                                                                      \
+  } while (0)
+
+struct ScanPlan {
+  int setup;          // index into the unique setups
+  Layout L;
+  size_t series_off;  // element offset in the batch series buffer
+  size_t nval_off;    // int offset of its valid-count table in the tables buffer
+};
+
+constexpr int kTuneTT[] = {32, 64, 128};
+
+}  // namespace
+
+extern "C" int frbx_batch_create(frbx_batch **out) {
+  if (!out) return FRBX_EINVAL;
+  *out = new frbx_batch();
+  return FRBX_OK;
+}
+
+extern "C" void frbx_batch_destroy(frbx_batch *b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (frbx_handle::Buf *x : {&b->desc, &b->tables, &b->series, &b->counters})
+    if (x->p) cudaFree(x->p);
+  if (b->e0) cudaEventDestroy(b->e0);
+  if (b->e1) cudaEventDestroy(b->e1);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  delete b;
+}
+
+extern "C" const char *frbx_batch_last_error(const frbx_batch *b) { return b ? b->err.c_str() : "null batch"; }
+
+extern "C" int frbx_batch_info(const frbx_batch *b, frbx_batch_stats *st) {
+  if (!b || !st) return FRBX_EINVAL;
+  std::memset(st, 0, sizeof(*st));
+  st->graph_captures = b->captures;
+  st->graph_replays = b->replays;
+  st->n_setups = (int32_t)b->last_tt.size();
+  for (size_t i = 0; i < b->last_tt.size() && i < 16; ++i) st->time_tile[i] = b->last_tt[i];
+  st->fit_ms = b->last_fit_ms;
+  st->launches = b->launches;
+  return FRBX_OK;
+}
+
+extern "C" int frbx_search_batch(frbx_batch *b, const frbx_scan *scans, int32_t n_scans, const double *dm,
+                                 int32_t n_dm, const int32_t *windows, int32_t n_win, const frbx_params *params,
+                                 frbx_results *results, void *cuda_stream) {
+  if (!b) return FRBX_EINVAL;
+  b->err.clear();
+  b->launches = 0;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (!scans || n_scans < 1 || n_scans > 4096 || !results) return bfail(b, FRBX_EINVAL, "need 1..4096 scans and results");
+  if (!dm || n_dm < 1) return bfail(b, FRBX_EINVAL, "need at least one DM trial");
+  if (!windows || n_win < 1 || n_win > frbx::kMaxWin) return bfail(b, FRBX_EINVAL, "need 1..16 windows");
+  for (int w = 0; w < n_win; ++w) {
+    if (windows[w] < 1) return bfail(b, FRBX_EINVAL, "window lengths must be >= 1");
+    for (int v = 0; v < w; ++v)
+      if (windows[v] == windows[w]) return bfail(b, FRBX_EINVAL, "window lengths must be distinct");
+  }
+  frbx_params p;
+  if (params) p = *params; else frbx_default_params(&p);
+  if (p.kernel < 0 || p.kernel > 2) return bfail(b, FRBX_EINVAL, "batched search runs kernels 0, 1 or 2");
+  // unique setups in order of first appearance
+  std::vector<frbx_handle *> setups;
+  std::vector<ScanPlan> plan((size_t)n_scans);
+  for (int i = 0; i < n_scans; ++i) {
+    const frbx_scan &sc = scans[i];
+    if (!sc.setup || !sc.vis_dev || sc.n_bl < 1 || sc.n_bl > frbx::kMaxBl || sc.T < 1 ||
+        ((uintptr_t)sc.vis_dev & 7u))
+      return bfail(b, FRBX_EINVAL, "scan " + std::to_string(i) + ": bad setup, cube, n_bl or T");
+    for (int c = 0; c < p.n_combo; ++c)
+      if (p.combos && sc.n_bl < 64 && (p.combos[c] >> sc.n_bl) != 0)
+        return bfail(b, FRBX_EINVAL, "scan " + std::to_string(i) + ": combo mask names a missing baseline");
+    auto it = std::find(setups.begin(), setups.end(), sc.setup);
+    plan[(size_t)i].setup = (int)(it - setups.begin());
+    if (it == setups.end()) setups.push_back(sc.setup);
+  }
+  if (setups.size() > 16) return bfail(b, FRBX_EINVAL, "at most 16 setups per batch");
+  // per setup: parameter checks and the shift table of the DM grid (h->dk, read by the fit)
+  std::vector<FitArgs> fa(setups.size());
+  std::vector<std::vector<int>> dkm(setups.size());
+  for (size_t g = 0; g < setups.size(); ++g) {
+    frbx_handle *h = setups[g];
+    h->err.clear();
+    int rc = check_params(h, &p, 64, &fa[g]);
+    if (!rc) rc = run_shift_table(h, dm, n_dm, &dkm[g], st);
+    if (rc) return bfail(b, rc, "setup " + std::to_string(g) + ": " + h->err);
+  }
+  // layouts, valid-segment counts, window offsets and series offsets of every scan; one device
+  // table: win_len[16] | per scan: win_off[16], n_valid[n_dm][n_win]
+  std::vector<int> tab(windows, windows + n_win);
+  tab.resize(frbx::kMaxWin, 0);
+  std::vector<size_t> woff_at((size_t)n_scans);
+  size_t series_total = 0;
+  for (int i = 0; i < n_scans; ++i) {
+    ScanPlan &sp = plan[(size_t)i];
+    const int T = scans[i].T;
+    long long stot = 0;
+    sp.L.win_len.assign(windows, windows + n_win);
+    for (int w = 0; w < n_win; ++w) {
+      sp.L.win_off.push_back((int)stot);
+      sp.L.win_step.push_back(window_step(windows[w]));
+      stot += n_slots(T, windows[w]);
+    }
+    if (stot > (1LL << 30)) return bfail(b, FRBX_EUNSUPPORTED, "too many segments per series");
+    sp.L.S_tot = (int)stot;
+    sp.L.n_valid.resize((size_t)n_dm * n_win);
+    for (int d = 0; d < n_dm; ++d)
+      for (int w = 0; w < n_win; ++w)
+        sp.L.n_valid[(size_t)d * n_win + w] = n_valid(T, windows[w], dkm[(size_t)sp.setup][(size_t)d]);
+    woff_at[(size_t)i] = tab.size();
+    tab.insert(tab.end(), sp.L.win_off.begin(), sp.L.win_off.end());
+    tab.resize(tab.size() + (size_t)(frbx::kMaxWin - n_win), 0);
+    sp.nval_off = tab.size();
+    tab.insert(tab.end(), sp.L.n_valid.begin(), sp.L.n_valid.end());
+    sp.series_off = series_total;
+    series_total += (size_t)scans[i].n_bl * n_dm * sp.L.S_tot;
+  }
+  FRBX_BCK(b, ensure(b->tables, sizeof(int) * tab.size()));
+  FRBX_BCK(b, cudaMemcpyAsync(b->tables.p, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice, st));
+  FRBX_BCK(b, ensure(b->series, sizeof(frbx_seg) * std::max<size_t>(series_total, 1)));
+  FRBX_BCK(b, ensure(b->counters, 256 * (setups.size() + 1)));
+  FRBX_BCK(b, ensure(b->desc, sizeof(frbx::BatchScan) * (size_t)n_scans * 2));
+  const int *d_tab = (const int *)b->tables.p;
+  frbx_seg *d_series = (frbx_seg *)b->series.p;
+  frbx::BatchScan *d_desc = (frbx::BatchScan *)b->desc.p;
+  unsigned int *d_cnt = (unsigned int *)b->counters.p;
+  if (!b->e0) FRBX_BCK(b, cudaEventCreate(&b->e0));
+  if (!b->e1) FRBX_BCK(b, cudaEventCreate(&b->e1));
+
+  // descriptors of the scans of setup g (in scan order), with time tile TT
+  auto make_desc = [&](int g, int TT, std::vector<frbx::BatchScan> *desc) {
+    long long item = 0;
+    desc->clear();
+    for (int i = 0; i < n_scans; ++i) {
+      if (plan[(size_t)i].setup != g) continue;
+      frbx::BatchScan d{};
+      d.vis = (const float2 *)scans[i].vis_dev;
+      d.out = d_series + plan[(size_t)i].series_off;
+      d.n_valid = d_tab + plan[(size_t)i].nval_off;
+      d.win_off = d_tab + woff_at[(size_t)i];
+      d.T = scans[i].T;
+      d.S_tot = plan[(size_t)i].L.S_tot;
+      d.n_bl = scans[i].n_bl;
+      d.n_tt = (scans[i].T + TT - 1) / TT;
+      d.item0 = item;
+      item += (long long)d.n_bl * d.n_tt * n_dm;
+      desc->push_back(d);
+    }
+    return item;
+  };
+  auto fit_args = [&](int g, int TT) {
+    FitArgs a;
+    std::memcpy(&a, &fa[(size_t)g], sizeof(a));
+    fill_fit_tables(setups[(size_t)g], &a, nullptr, 0, n_dm);
+    a.n_win = n_win;
+    a.win_len = d_tab;
+    a.win_off = nullptr;
+    a.n_valid = nullptr;
+    a.TT = TT;
+    a.tile = 64;
+    return a;
+  };
+
+  // time tile per setup: measured once per (setup shape, DM count, windows, kernel) and kept.
+  // Every candidate fits the same leading stretch of the setup's items (4096 AP-baselines of
+  // every DM trial, or all of them), twice; the faster minimum wins.
+  b->last_tt.assign(setups.size(), 64);
+  std::vector<frbx::BatchScan> desc;
+  for (size_t g = 0; g < setups.size(); ++g) {
+    frbx_handle *h = setups[g];
+    std::string tkey = std::to_string(h->N) + "x" + std::to_string(h->J) + "/" + std::to_string(h->Ls) + "/" +
+                       std::to_string(h->Lm) + "/" + std::to_string(n_dm);
+    for (int w = 0; w < n_win; ++w) tkey += "," + std::to_string(windows[w]);
+    tkey += "/" + std::to_string(p.kernel) + "/" + std::to_string(fa[g].m_len) + "x" + std::to_string(fa[g].q_len);
+    auto hit = b->tuned_tt.find(tkey);
+    if (hit != b->tuned_tt.end()) {
+      b->last_tt[g] = hit->second;
+      continue;
+    }
+    float best_ms = 1e30f;
+    int best_tt = 64;
+    for (int TT : kTuneTT) {
+      const long long total = make_desc((int)g, TT, &desc);
+      FRBX_BCK(b, cudaMemcpyAsync(d_desc, desc.data(), sizeof(frbx::BatchScan) * desc.size(), cudaMemcpyHostToDevice,
+                                  st));
+      const FitArgs a = fit_args((int)g, TT);
+      const long long sample = std::min<long long>(total, (long long)n_dm * (4096 / TT));
+      float ms_min = 1e30f;
+      for (int rep = 0; rep < 2; ++rep) {
+        FRBX_BCK(b, cudaMemsetAsync(d_cnt, 0, sizeof(unsigned int), st));
+        FRBX_BCK(b, cudaEventRecord(b->e0, st));
+        cudaError_t e = frbx::launch_fit_batch(a, d_desc, (int)desc.size(), sample, d_cnt, p.kernel, 0, st,
+                                               &b->launches);
+        if (e == cudaErrorInvalidConfiguration)
+          return bfail(b, FRBX_EUNSUPPORTED, "fit kernel does not fit setup " + std::to_string(g));
+        FRBX_BCK(b, e);
+        FRBX_BCK(b, cudaEventRecord(b->e1, st));
+        FRBX_BCK(b, cudaEventSynchronize(b->e1));
+        float ms = 0.f;
+        FRBX_BCK(b, cudaEventElapsedTime(&ms, b->e0, b->e1));
+        ms_min = std::min(ms_min, ms);
+      }
+      if (ms_min < best_ms) {
+        best_ms = ms_min;
+        best_tt = TT;
+      }
+    }
+    b->tuned_tt[tkey] = best_tt;
+    b->last_tt[g] = best_tt;
+  }
+
+  // descriptors with the chosen tiles; the graph is re-captured only when they change
+  const size_t half = (size_t)n_scans;  // second half of the descriptor buffer: graph copies
+  std::vector<frbx::BatchScan> all;
+  std::vector<long long> totals(setups.size());
+  std::vector<size_t> first(setups.size());
+  for (size_t g = 0; g < setups.size(); ++g) {
+    totals[g] = make_desc((int)g, b->last_tt[g], &desc);
+    if (totals[g] > 0x7fffffffLL) return bfail(b, FRBX_EUNSUPPORTED, "too many work items for one setup");
+    first[g] = all.size();
+    all.insert(all.end(), desc.begin(), desc.end());
+  }
+  FRBX_BCK(b, cudaMemcpyAsync(d_desc + half, all.data(), sizeof(frbx::BatchScan) * all.size(), cudaMemcpyHostToDevice,
+                              st));
+  std::string key = std::to_string(n_scans) + ":" + std::to_string(n_dm) + ":" + std::to_string(p.kernel) + ":" +
+                    std::to_string((uintptr_t)b->desc.p) + ":" + std::to_string((uintptr_t)b->counters.p);
+  for (size_t g = 0; g < setups.size(); ++g) {
+    // the launch parameters baked into the graph, byte for byte
+    const FitArgs a = fit_args((int)g, b->last_tt[g]);
+    key += "|" + std::to_string(totals[g]) + "/" + std::to_string(first[g]) + "/";
+    key.append(reinterpret_cast<const char *>(&a), sizeof(a));
+  }
+  if (b->key != key || !b->exec) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    b->key.clear();
+    // the graph is recorded on a private stream and launched on the caller's
+    if (!b->cap) FRBX_BCK(b, cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+    cudaStream_t cs = b->cap;
+    FRBX_BCK(b, cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+    cudaError_t ce = cudaSuccess;
+    int64_t graph_launches = 0;
+    for (size_t g = 0; g < setups.size() && ce == cudaSuccess; ++g) {
+      unsigned int *cnt = d_cnt + 64 * (g + 1);
+      ce = cudaMemsetAsync(cnt, 0, sizeof(unsigned int), cs);
+      if (ce == cudaSuccess) {
+        const size_t nd = (g + 1 < setups.size() ? first[g + 1] : all.size()) - first[g];
+        ce = frbx::launch_fit_batch(fit_args((int)g, b->last_tt[g]), d_desc + half + first[g], (int)nd, totals[g],
+                                    cnt, p.kernel, 0, cs, &graph_launches);
+      }
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(cs, &graph);
+    if (ce != cudaSuccess || ee != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return bfail(b, ce == cudaErrorInvalidConfiguration ? FRBX_EUNSUPPORTED : FRBX_ECUDA,
+                   std::string("fit graph capture: ") + cudaGetErrorString(ce != cudaSuccess ? ce : ee));
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&b->exec, graph, 0);
+    if (ie != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      b->exec = nullptr;
+      cudaGetLastError();
+      return bfail(b, FRBX_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie));
+    }
+    b->graph = graph;
+    b->graph_kernels = graph_launches;
+    b->key = key;
+    ++b->captures;
+  } else {
+    ++b->replays;
+  }
+  FRBX_BCK(b, cudaEventRecord(b->e0, st));
+  FRBX_BCK(b, cudaGraphLaunch(b->exec, st));
+  FRBX_BCK(b, cudaEventRecord(b->e1, st));
+  FRBX_BCK(b, cudaEventSynchronize(b->e1));
+  {
+    float ms = 0.f;
+    FRBX_BCK(b, cudaEventElapsedTime(&ms, b->e0, b->e1));
+    b->last_fit_ms = ms;
+  }
+  b->launches += b->graph_kernels;
+
+  // per scan: Eq. 6 and threshold on the device, then the host extraction, as in frbx_search;
+  // the scan's window tables go to the head of its setup's small buffer in that layout
+  bool trunc = false;
+  for (int i = 0; i < n_scans; ++i) {
+    frbx_handle *h = setups[(size_t)plan[(size_t)i].setup];
+    const Layout &L = plan[(size_t)i].L;
+    std::vector<int> t2(3 * frbx::kMaxWin, 0);
+    for (int w = 0; w < n_win; ++w) {
+      t2[(size_t)w] = windows[w];
+      t2[(size_t)frbx::kMaxWin + w] = L.win_off[(size_t)w];
+      t2[(size_t)2 * frbx::kMaxWin + w] = L.win_step[(size_t)w];
+    }
+    t2.insert(t2.end(), L.n_valid.begin(), L.n_valid.end());
+    h->err.clear();
+    h->launches = 0;
+    int rc = FRBX_OK;
+    if (ensure(h->small, sizeof(int) * t2.size() + 4096) != cudaSuccess ||
+        cudaMemcpyAsync(h->small.p, t2.data(), sizeof(int) * t2.size(), cudaMemcpyHostToDevice, st) != cudaSuccess) {
+      cudaGetLastError();
+      return bfail(b, FRBX_ECUDA, "scan " + std::to_string(i) + ": table upload failed");
+    }
+    for (cudaEvent_t &ev : h->ev)
+      if (!ev && cudaEventCreate(&ev) != cudaSuccess) return bfail(b, FRBX_ECUDA, "cudaEventCreate failed");
+    for (int k = 0; k < 4; ++k) cudaEventRecord(h->ev[k], st);
+    rc = finish_search(h, d_series + plan[(size_t)i].series_off, scans[i].n_bl, scans[i].T, dm, n_dm, n_win, L,
+                       (const int *)h->small.p, p, &results[i], st);
+    b->launches += h->launches;
+    if (rc == FRBX_ETRUNC) trunc = true;
+    else if (rc) return bfail(b, rc, "scan " + std::to_string(i) + ": " + h->err);
+  }
+  if (trunc) return bfail(b, FRBX_ETRUNC, "an output array was too small");
   return FRBX_OK;
 }

@@ -20,6 +20,16 @@ constexpr int kMaxWin = 16;
 constexpr int kMaxBl = 64;
 constexpr int kFitThreads = 256;
 
+// One scan of a batched fit: its cube, output series, valid-segment table and first work item.
+struct BatchScan {
+  const float2 *vis;       // [n_bl][T][C]
+  frbx_seg *out;           // [n_bl][n_dm][S_tot]
+  const int *n_valid;      // [n_dm][n_win]
+  const int *win_off;      // [n_win] first slot of each window in a series of this scan
+  int T, S_tot, n_bl, n_tt;
+  long long item0;         // items [item0, item0 + n_bl * n_tt * n_dm) belong to this scan
+};
+
 // Segment source of a fit launch: either the implicit half-overlap layout of a
 // (baseline, DM) series, or an explicit device list of (bl, d, l, k0) rows.
 struct FitArgs {
@@ -58,6 +68,10 @@ struct FitArgs {
 // Launchers (kernels_fit.cu).  Return a cudaError_t.
 cudaError_t launch_fit(const FitArgs &a, int n_bl, bool list_mode, int kernel,
                        cudaStream_t st, int64_t *launches);
+// Persistent fit over the work items of several scans of one setup (items claimed from *counter,
+// which must be zero at launch); ctas_per_sm 0 = as many as fit.
+cudaError_t launch_fit_batch(const FitArgs &a, const BatchScan *scans_dev, int n_scans, long long total_items,
+                             unsigned int *counter, int kernel, int ctas_per_sm, cudaStream_t st, int64_t *launches);
 bool fft_supported(int Ls, int Lm, int J);
 void set_fft_constants();
 // kernels_mma.cu: tensor-core (tcgen05, BF16) form of the MBD transform
@@ -110,6 +124,8 @@ cudaError_t launch_cal_channels(const double2 *xsum, const float2 *wrot, int n_b
 // kernels_fft.cu
 cudaError_t launch_fit_fft(const FitArgs &a, int n_bl, bool list_mode, cudaStream_t st,
                            int64_t *launches);
+cudaError_t launch_fit_fft_batch(const FitArgs &a, const BatchScan *scans_dev, int n_scans, long long total_items,
+                                 unsigned int *counter, int ctas_per_sm, cudaStream_t st, int64_t *launches);
 size_t max_smem_optin();
 bool fit_grid(const FitArgs &a, int n_bl, bool list_mode, dim3 *grid);
 

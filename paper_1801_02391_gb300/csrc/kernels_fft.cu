@@ -35,8 +35,10 @@ __host__ __device__ inline FftSmem fft_smem_layout(int N, int Ls, int Lm, int J1
   return l;
 }
 
-template <int OCC, bool kFull>
-__global__ void __launch_bounds__(kFftThreads, 4) k_fit_fft(const __grid_constant__ FitArgs a, int list) {
+template <int OCC, bool kFull, bool kBatch>
+__global__ void __launch_bounds__(kFftThreads, 4)
+    k_fit_fft(const __grid_constant__ FitArgs a, int list, const BatchScan *scans, int n_scans, long long total,
+              unsigned int *counter) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int N = a.N, Ls = a.Ls, Lm = a.Lm;
   const int PS = Ls >> 5, PM = Lm >> 5;
@@ -57,17 +59,30 @@ __global__ void __launch_bounds__(kFftThreads, 4) k_fit_fft(const __grid_constan
   }
   for (int i = threadIdx.x; i < N * PM; i += blockDim.x) mtw[i] = a.mbd_tw[i];
   __shared__ TileWin tw;
-  if (!list) tile_windows(a, tw);
-  __syncthreads();
+  __shared__ long long s_item;
 
+  for (int pass = 0;; ++pass) {
+    ItemCtx c;
+    if (kBatch) {
+      if (threadIdx.x == 0) s_item = (long long)atomicAdd(counter, 1u);
+      __syncthreads();
+      const long long item = s_item;
+      if (item >= total) break;
+      c = batch_item(a, scans, n_scans, item);
+    } else {
+      if (pass > 0) break;
+      c = plain_item(a);
+    }
+    if (!list) tile_windows(a, c, tw);
+    __syncthreads();
   for (int it = 0;; ++it) {
     Seg s;
-    if (!tile_segment(a, list, it, tw, s)) break;
+    if (!tile_segment(a, list, it, tw, c, s)) break;
     if (!s.valid) {
-      if (threadIdx.x == 0) write_fit(a, s, -1.f, 0);
+      if (threadIdx.x == 0) write_fit(a, c.out, s, -1.f, 0);
       continue;
     }
-    gather_segment(a, s, X, L.xs);
+    gather_segment(a, c, s, X, L.xs);
     __syncthreads();
 
     // SBD transform, task (n, m1)
@@ -120,7 +135,9 @@ __global__ void __launch_bounds__(kFftThreads, 4) k_fit_fft(const __grid_constan
       if (key != 0u) better(bp, bi, __uint_as_float(key & ~63u), m * Lm + q1 + PM * (32 - (int)(key & 63u)));
     }
     block_best(bp, bi, rp, ri);
-    if (threadIdx.x == 0) write_fit(a, s, bp, bi);
+    if (threadIdx.x == 0) write_fit(a, c.out, s, bp, bi);
+  }
+    __syncthreads();  // the tile table and the item slot are reused by the next item
   }
 }
 
@@ -131,11 +148,14 @@ void set_fft_constants() {
 
 bool fft_supported(int Ls, int Lm, int J) { return Ls % 32 == 0 && Lm % 32 == 0 && J <= Ls; }
 
-template <int OCC, bool kFull>
-static cudaError_t launch_one(const FitArgs &a, dim3 grid, size_t smem, int list, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(k_fit_fft<OCC, kFull>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+template <int OCC, bool kFull, bool kBatch>
+static cudaError_t launch_one(const FitArgs &a, dim3 grid, size_t smem, int list, cudaStream_t st,
+                              const BatchScan *scans = nullptr, int n_scans = 0, long long total = 0,
+                              unsigned int *counter = nullptr) {
+  cudaError_t e = cudaFuncSetAttribute(k_fit_fft<OCC, kFull, kBatch>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
   if (e != cudaSuccess) return e;
-  k_fit_fft<OCC, kFull><<<grid, kFftThreads, smem, st>>>(a, list);
+  k_fit_fft<OCC, kFull, kBatch><<<grid, kFftThreads, smem, st>>>(a, list, scans, n_scans, total, counter);
   return cudaGetLastError();
 }
 
@@ -149,9 +169,29 @@ cudaError_t launch_fit_fft(const FitArgs &a, int n_bl, bool list_mode, cudaStrea
   const bool full = a.m_lo == 0 && a.m_len == a.Ls && a.q_lo == 0 && a.q_len == a.Lm;
   const int list = list_mode ? 1 : 0;
   cudaError_t e;
-  if (a.occ == 1) e = full ? launch_one<1, true>(a, grid, smem, list, st) : launch_one<1, false>(a, grid, smem, list, st);
-  else if (a.occ == 2) e = full ? launch_one<2, true>(a, grid, smem, list, st) : launch_one<2, false>(a, grid, smem, list, st);
-  else e = full ? launch_one<4, true>(a, grid, smem, list, st) : launch_one<4, false>(a, grid, smem, list, st);
+  if (a.occ == 1) e = full ? launch_one<1, true, false>(a, grid, smem, list, st) : launch_one<1, false, false>(a, grid, smem, list, st);
+  else if (a.occ == 2) e = full ? launch_one<2, true, false>(a, grid, smem, list, st) : launch_one<2, false, false>(a, grid, smem, list, st);
+  else e = full ? launch_one<4, true, false>(a, grid, smem, list, st) : launch_one<4, false, false>(a, grid, smem, list, st);
+  ++*launches;
+  return e;
+}
+
+cudaError_t launch_fit_fft_batch(const FitArgs &a, const BatchScan *scans, int n_scans, long long total,
+                                 unsigned int *counter, int ctas_per_sm, cudaStream_t st, int64_t *launches) {
+  if (!fft_supported(a.Ls, a.Lm, a.J) || a.occ > 4 || a.occ < 1) return cudaErrorInvalidConfiguration;
+  const size_t smem = fft_smem_layout(a.N, a.Ls, a.Lm, a.J1).bytes;
+  if (smem > max_smem_optin()) return cudaErrorInvalidConfiguration;
+  if (total <= 0) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int per_sm = ctas_per_sm > 0 ? ctas_per_sm : 4;
+  const dim3 grid((unsigned)(sms * per_sm));
+  const bool full = a.m_lo == 0 && a.m_len == a.Ls && a.q_lo == 0 && a.q_len == a.Lm;
+  cudaError_t e;
+  if (a.occ == 1) e = full ? launch_one<1, true, true>(a, grid, smem, 0, st, scans, n_scans, total, counter) : launch_one<1, false, true>(a, grid, smem, 0, st, scans, n_scans, total, counter);
+  else if (a.occ == 2) e = full ? launch_one<2, true, true>(a, grid, smem, 0, st, scans, n_scans, total, counter) : launch_one<2, false, true>(a, grid, smem, 0, st, scans, n_scans, total, counter);
+  else e = full ? launch_one<4, true, true>(a, grid, smem, 0, st, scans, n_scans, total, counter) : launch_one<4, false, true>(a, grid, smem, 0, st, scans, n_scans, total, counter);
   ++*launches;
   return e;
 }

@@ -6,6 +6,8 @@
 //  * k_fit_direct: direct DFT sums from shared-memory twiddle tables; any grid size.
 //  * k_fit_fft (kernels_fft.cu): four-step decomposition with 32-point register FFTs;
 //                  needs Ls and Lm multiples of 32.
+#include <algorithm>
+
 #include "fit_common.cuh"
 
 namespace frbx {
@@ -13,7 +15,10 @@ namespace frbx {
 // --------------------------------------------------------------------------------------
 // Direct-DFT kernel (any grid)
 // --------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kFitThreads) k_fit_direct(FitArgs a, int list) {
+template <bool kBatch>
+__global__ void __launch_bounds__(kFitThreads)
+    k_fit_direct(const __grid_constant__ FitArgs a, int list, const BatchScan *scans, int n_scans, long long total,
+                 unsigned int *counter) {
   extern __shared__ __align__(16) unsigned char smem[];
   float2 *X = reinterpret_cast<float2 *>(smem);  // [C]
   float2 *Y = X + a.C;                           // [N][Ls]
@@ -27,18 +32,31 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_direct(FitArgs a, int list)
   for (int i = threadIdx.x; i < a.Lm; i += blockDim.x) twm[i] = a.tw_m[i];
   for (int i = threadIdx.x; i < a.N; i += blockDim.x) gsh[i] = a.g[i];
   __shared__ TileWin tw;
-  if (!list) tile_windows(a, tw);
-  __syncthreads();
+  __shared__ long long s_item;
 
   const int Ls = a.Ls, Lm = a.Lm, J = a.J, N = a.N;
+  for (int pass = 0;; ++pass) {
+    ItemCtx c;
+    if (kBatch) {
+      if (threadIdx.x == 0) s_item = (long long)atomicAdd(counter, 1u);
+      __syncthreads();
+      const long long item = s_item;
+      if (item >= total) break;
+      c = batch_item(a, scans, n_scans, item);
+    } else {
+      if (pass > 0) break;
+      c = plain_item(a);
+    }
+    if (!list) tile_windows(a, c, tw);
+    __syncthreads();
   for (int it = 0;; ++it) {
     Seg s;
-    if (!tile_segment(a, list, it, tw, s)) break;
+    if (!tile_segment(a, list, it, tw, c, s)) break;
     if (!s.valid) {
-      if (threadIdx.x == 0) write_fit(a, s, -1.f, 0);
+      if (threadIdx.x == 0) write_fit(a, c.out, s, -1.f, 0);
       continue;
     }
-    gather_segment(a, s, X, J);
+    gather_segment(a, c, s, X, J);
     __syncthreads();
     // Eq. 5, sum over j = 1 .. J-1 for every (n, m)
     for (int o = threadIdx.x; o < N * Ls; o += blockDim.x) {
@@ -63,8 +81,10 @@ __global__ void __launch_bounds__(kFitThreads) k_fit_direct(FitArgs a, int list)
       }
     }
     block_best(bp, bi, rp, ri);
-    if (threadIdx.x == 0) write_fit(a, s, bp, bi);
+    if (threadIdx.x == 0) write_fit(a, c.out, s, bp, bi);
     __syncthreads();
+  }
+    __syncthreads();  // the tile table and the item slot are reused by the next item
   }
 }
 
@@ -110,9 +130,29 @@ cudaError_t launch_fit(const FitArgs &a, int n_bl, bool list_mode, int kernel, c
   dim3 grid;
   if (!fit_grid(a, n_bl, list_mode, &grid)) return cudaErrorInvalidConfiguration;
   if (grid.x == 0 || grid.y == 0 || grid.z == 0) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_fit_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_fit_direct<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_fit_direct<<<grid, kFitThreads, smem, st>>>(a, list_mode ? 1 : 0);
+  k_fit_direct<false><<<grid, kFitThreads, smem, st>>>(a, list_mode ? 1 : 0, nullptr, 0, 0, nullptr);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fit_batch(const FitArgs &a, const BatchScan *scans, int n_scans, long long total,
+                             unsigned int *counter, int kernel, int ctas_per_sm, cudaStream_t st, int64_t *launches) {
+  const bool use_fft = kernel == 2 || (kernel == 0 && fft_supported(a.Ls, a.Lm, a.J) && a.occ <= 4);
+  if (use_fft) return launch_fit_fft_batch(a, scans, n_scans, total, counter, ctas_per_sm, st, launches);
+  const size_t smem = direct_smem(a);
+  if (smem > max_smem_optin()) return cudaErrorInvalidConfiguration;
+  if (total <= 0) return cudaSuccess;
+  int dev = 0, sms = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = cudaFuncSetAttribute(k_fit_direct<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fit_direct<true>, kFitThreads, smem);
+  if (e != cudaSuccess) return e;
+  const int per_sm = ctas_per_sm > 0 ? std::min(ctas_per_sm, std::max(occ, 1)) : std::max(occ, 1);
+  k_fit_direct<true><<<(unsigned)(sms * per_sm), kFitThreads, smem, st>>>(a, 0, scans, n_scans, total, counter);
   ++*launches;
   return cudaGetLastError();
 }

@@ -290,7 +290,6 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
               off[q] = c < C ? (k0 + __ldg(dk + c)) * C + c : 0;
               acc[q] = make_float2(0.f, 0.f);
             }
-#pragma unroll 4
             for (int r = 0; r < l; ++r) {
 #pragma unroll
               for (int q = 0; q < kGatherBatch; ++q) {
@@ -434,51 +433,28 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
           if (!ok) continue;
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t t_row = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(s * mm.NC);
-          for (int p0 = part * qpart; p0 < (part + 1) * qpart; p0 += 32) {
-            const int nq = min(32, (part + 1) * qpart - p0);  // 8, 16 or 32 columns
-            uint32_t re[32], im[32];
-            if (nq == 32) {
-              asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                           : "=r"(re[0]), "=r"(re[1]), "=r"(re[2]), "=r"(re[3]), "=r"(re[4]), "=r"(re[5]), "=r"(re[6]), "=r"(re[7]),
-                             "=r"(re[8]), "=r"(re[9]), "=r"(re[10]), "=r"(re[11]), "=r"(re[12]), "=r"(re[13]), "=r"(re[14]), "=r"(re[15]),
-                             "=r"(re[16]), "=r"(re[17]), "=r"(re[18]), "=r"(re[19]), "=r"(re[20]), "=r"(re[21]), "=r"(re[22]), "=r"(re[23]),
-                             "=r"(re[24]), "=r"(re[25]), "=r"(re[26]), "=r"(re[27]), "=r"(re[28]), "=r"(re[29]), "=r"(re[30]), "=r"(re[31])
-                           : "r"(t_row + (uint32_t)p0));
-              asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                           : "=r"(im[0]), "=r"(im[1]), "=r"(im[2]), "=r"(im[3]), "=r"(im[4]), "=r"(im[5]), "=r"(im[6]), "=r"(im[7]),
-                             "=r"(im[8]), "=r"(im[9]), "=r"(im[10]), "=r"(im[11]), "=r"(im[12]), "=r"(im[13]), "=r"(im[14]), "=r"(im[15]),
-                             "=r"(im[16]), "=r"(im[17]), "=r"(im[18]), "=r"(im[19]), "=r"(im[20]), "=r"(im[21]), "=r"(im[22]), "=r"(im[23]),
-                             "=r"(im[24]), "=r"(im[25]), "=r"(im[26]), "=r"(im[27]), "=r"(im[28]), "=r"(im[29]), "=r"(im[30]), "=r"(im[31])
-                           : "r"(t_row + (uint32_t)(half + p0)));
-            } else if (nq == 16) {
-              asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                           : "=r"(re[0]), "=r"(re[1]), "=r"(re[2]), "=r"(re[3]), "=r"(re[4]), "=r"(re[5]), "=r"(re[6]), "=r"(re[7]),
-                             "=r"(re[8]), "=r"(re[9]), "=r"(re[10]), "=r"(re[11]), "=r"(re[12]), "=r"(re[13]), "=r"(re[14]), "=r"(re[15])
-                           : "r"(t_row + (uint32_t)p0));
-              asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                           : "=r"(im[0]), "=r"(im[1]), "=r"(im[2]), "=r"(im[3]), "=r"(im[4]), "=r"(im[5]), "=r"(im[6]), "=r"(im[7]),
-                             "=r"(im[8]), "=r"(im[9]), "=r"(im[10]), "=r"(im[11]), "=r"(im[12]), "=r"(im[13]), "=r"(im[14]), "=r"(im[15])
-                           : "r"(t_row + (uint32_t)(half + p0)));
-            } else {
-              asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                           : "=r"(re[0]), "=r"(re[1]), "=r"(re[2]), "=r"(re[3]), "=r"(re[4]), "=r"(re[5]), "=r"(re[6]), "=r"(re[7])
-                           : "r"(t_row + (uint32_t)p0));
-              asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                           : "=r"(im[0]), "=r"(im[1]), "=r"(im[2]), "=r"(im[3]), "=r"(im[4]), "=r"(im[5]), "=r"(im[6]), "=r"(im[7])
-                           : "r"(t_row + (uint32_t)(half + p0)));
-            }
+          for (int p0 = part * qpart; p0 < (part + 1) * qpart; p0 += 16) {
+            uint32_t re[16], im[16];
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                         : "=r"(re[0]), "=r"(re[1]), "=r"(re[2]), "=r"(re[3]), "=r"(re[4]), "=r"(re[5]), "=r"(re[6]),
+                           "=r"(re[7]), "=r"(re[8]), "=r"(re[9]), "=r"(re[10]), "=r"(re[11]), "=r"(re[12]), "=r"(re[13]),
+                           "=r"(re[14]), "=r"(re[15])
+                         : "r"(t_row + (uint32_t)p0));
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                         : "=r"(im[0]), "=r"(im[1]), "=r"(im[2]), "=r"(im[3]), "=r"(im[4]), "=r"(im[5]), "=r"(im[6]),
+                           "=r"(im[7]), "=r"(im[8]), "=r"(im[9]), "=r"(im[10]), "=r"(im[11]), "=r"(im[12]), "=r"(im[13]),
+                           "=r"(im[14]), "=r"(im[15])
+                         : "r"(t_row + (uint32_t)(half + p0)));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             unsigned key = 0u;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              if (j < nq) {
-                const float gr = __uint_as_float(re[j]), gi = __uint_as_float(im[j]);
-                const float pw = fmaf(gr, gr, gi * gi);
-                key = max(key, (__float_as_uint(pw) & ~63u) | (unsigned)(32 - j));
-              }
+            for (int j = 0; j < 16; ++j) {
+              const float gr = __uint_as_float(re[j]), gi = __uint_as_float(im[j]);
+              const float pw = fmaf(gr, gr, gi * gi);
+              key = max(key, (__float_as_uint(pw) & ~31u) | (unsigned)(16 - j));
             }
-            const int q = c * half + p0 + 32 - (int)(key & 63u);
-            const float pk = __uint_as_float(key & ~63u);
+            const int q = c * half + p0 + 16 - (int)(key & 31u);
+            const float pk = __uint_as_float(key & ~31u);
             if (pk > bp || (pk == bp && q < bq)) {
               bp = pk;
               bq = q;

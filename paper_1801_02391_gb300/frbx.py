@@ -86,6 +86,15 @@ class frbx_results(ctypes.Structure):
                 ("series_cap", c_i64), ("series_count", c_i64), ("events_baseline_count", c_i64)]
 
 
+class frbx_scan(ctypes.Structure):
+    _fields_ = [("setup", c_vp), ("vis_dev", c_vp), ("n_bl", c_i32), ("T", c_i32)]
+
+
+class frbx_batch_stats(ctypes.Structure):
+    _fields_ = [("graph_captures", c_i32), ("graph_replays", c_i32), ("n_setups", c_i32),
+                ("time_tile", c_i32 * 16), ("reserved", c_i32), ("fit_ms", c_f64), ("launches", c_i64)]
+
+
 assert ctypes.sizeof(frbx_cand) == CAND_DTYPE.itemsize == 80
 assert ctypes.sizeof(frbx_event) == EVENT_DTYPE.itemsize == 28
 
@@ -110,6 +119,12 @@ SIGNATURES = {
                                P(c_f64), c_vp]),
     "frbx_fit_segments_noalloc": (c_i32, [P(frbx_setup), c_vp, c_i32, c_i32, P(c_f64), c_i32, P(c_i32), c_i64,
                                           c_vp, c_vp]),
+    "frbx_batch_create": (c_i32, [P(c_vp)]),
+    "frbx_batch_destroy": (None, [c_vp]),
+    "frbx_batch_last_error": (ctypes.c_char_p, [c_vp]),
+    "frbx_batch_info": (c_i32, [c_vp, P(frbx_batch_stats)]),
+    "frbx_search_batch": (c_i32, [c_vp, P(frbx_scan), c_i32, P(c_f64), c_i32, P(c_i32), c_i32, P(frbx_params),
+                                  P(frbx_results), c_vp]),
     "frbx_extract_events": (c_i32, [c_vp, c_i64, c_i32, c_i32, c_i32, P(c_i32), c_i32, c_i32, c_i32, c_i32,
                                     c_vp, c_i64, P(c_i64), c_vp, c_i64, P(c_i64), c_vp, c_i64, P(c_i64)]),
 }
@@ -212,6 +227,38 @@ def _vis_arg(vis):
         pass
     a = np.ascontiguousarray(vis, np.complex64)
     return a.ctypes.data_as(c_vp), 0, a, a.shape
+
+
+_RESULT_KINDS = (("pulses", "CAND"), ("groups", "GROUP"), ("combined", "CAND"), ("pulses_dm", "CAND"),
+                 ("events", "EVENT"))
+
+
+def _default_caps(caps, want_events, want_pre_merge):
+    caps = dict(caps or {})
+    caps.setdefault("pulses", 1 << 16)
+    caps.setdefault("groups", 1 << 16)
+    caps.setdefault("combined", 1 << 16)
+    caps.setdefault("pulses_dm", 1 << 18 if want_pre_merge else 0)
+    caps.setdefault("events", 1 << 20 if want_events else 0)
+    return caps
+
+
+def _result_buffers(caps):
+    """Host output arrays of the sizes in caps and a frbx_results pointing at them."""
+    dt = {"CAND": CAND_DTYPE, "GROUP": GROUP_DTYPE, "EVENT": EVENT_DTYPE}
+    bufs = {k: np.zeros(caps[k], dt[kind]) for k, kind in _RESULT_KINDS}
+    r = frbx_results()
+    for k, arr in bufs.items():
+        setattr(r, k, arr.ctypes.data_as(c_vp) if arr.size else None)
+        setattr(r, k + "_cap", arr.size)
+    return bufs, r
+
+
+def _collect(bufs, r):
+    out = {k: bufs[k][:int(getattr(r, k + "_count"))].copy() if bufs[k].size else None for k in bufs}
+    out["counts"] = {k: int(getattr(r, k + "_count")) for k in bufs}
+    out["counts"]["events_baseline"] = int(r.events_baseline_count)
+    return out
 
 
 class Handle:
@@ -342,21 +389,9 @@ class Handle:
         p, cm = self._params(threshold, nwin_min, sbd_win_ns, mbd_win_ns, combos, kernel)
         _, S_tot = frbx_series_layout(T, win)
         n_series = n_bl * len(dm) * S_tot
-        caps = dict(caps or {})
-        caps.setdefault("pulses", 1 << 16)
-        caps.setdefault("groups", 1 << 16)
-        caps.setdefault("combined", 1 << 16)
-        caps.setdefault("pulses_dm", 1 << 18 if want_pre_merge else 0)
-        caps.setdefault("events", 1 << 20 if want_events else 0)
+        caps = _default_caps(caps, want_events, want_pre_merge)
         for attempt in range(2):
-            bufs = {"pulses": np.zeros(caps["pulses"], CAND_DTYPE), "groups": np.zeros(caps["groups"], GROUP_DTYPE),
-                    "combined": np.zeros(caps["combined"], CAND_DTYPE),
-                    "pulses_dm": np.zeros(caps["pulses_dm"], CAND_DTYPE),
-                    "events": np.zeros(caps["events"], EVENT_DTYPE)}
-            r = frbx_results()
-            for k, arr in bufs.items():
-                setattr(r, k, arr.ctypes.data_as(c_vp) if arr.size else None)
-                setattr(r, k + "_cap", arr.size)
+            bufs, r = _result_buffers(caps)
             ser_host = pn_host = None
             if series_out is not None or pnorm_out is not None:
                 r.series_on_device = 1
@@ -379,15 +414,116 @@ class Handle:
                 continue
             _check(self.h, rc)
             break
-        out = {k: bufs[k][:int(getattr(r, k + "_count"))].copy() if bufs[k].size else None for k in bufs}
-        out["counts"] = {k: int(getattr(r, k + "_count")) for k in bufs}
-        out["counts"]["events_baseline"] = int(r.events_baseline_count)
+        out = _collect(bufs, r)
         out["S_tot"] = S_tot
         out["launches"] = self.launch_count()
         if ser_host is not None:
             out["series"] = ser_host.reshape(n_bl, len(dm), S_tot)
             out["pnorm"] = pn_host.reshape(n_bl, len(dm), S_tot)
         return out
+
+
+class Batch:
+    """Batched search over many device-resident scans (frbx_batch_* / frbx_search_batch).
+
+    The object keeps the captured fit graph and the tuned time tiles between calls: a second
+    call with scans of the same shapes in the same buffers replays the graph."""
+
+    def __init__(self):
+        b = c_vp()
+        rc = load().frbx_batch_create(ctypes.byref(b))
+        if rc != FRBX_OK:
+            raise FrbxError(rc, "frbx_batch_create failed")
+        self.b = b
+
+    def close(self):
+        if getattr(self, "b", None):
+            load().frbx_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def last_error(self) -> str:
+        return load().frbx_batch_last_error(self.b).decode()
+
+    def info(self) -> dict:
+        st = frbx_batch_stats()
+        rc = load().frbx_batch_info(self.b, ctypes.byref(st))
+        if rc != FRBX_OK:
+            raise FrbxError(rc, "frbx_batch_info")
+        return {"graph_captures": st.graph_captures, "graph_replays": st.graph_replays,
+                "time_tile": list(st.time_tile[:st.n_setups]), "fit_ms": st.fit_ms, "launches": st.launches}
+
+    def search(self, scans, dms, windows, threshold=3.0, nwin_min=3, combos=(), sbd_win_ns=None,
+               mbd_win_ns=None, kernel=0, want_series=False, want_events=False, want_pre_merge=False,
+               caps=None, stream=None):
+        """scans: sequence of (Handle, complex64 CUDA tensor [n_bl][T][C]).  Returns one dict per
+        scan, as Handle.search does."""
+        lib = load()
+        keep = []
+        arr = (frbx_scan * len(scans))()
+        shapes = []
+        for i, (h, vis) in enumerate(scans):
+            vp, on_dev, k, shape = _vis_arg(vis)
+            if not on_dev:
+                raise ValueError("batched scans must be CUDA tensors")
+            assert shape[2] == h.C, "cube does not match its setup"
+            keep.append(k)
+            arr[i].setup = h.h
+            arr[i].vis_dev = vp
+            arr[i].n_bl, arr[i].T = shape[0], shape[1]
+            shapes.append(shape)
+        dm = np.ascontiguousarray(dms, np.float64)
+        win = np.ascontiguousarray(windows, np.int32)
+        p, cm = scans[0][0]._params(threshold, nwin_min, sbd_win_ns, mbd_win_ns, combos, kernel)
+        caps_l = [_default_caps(caps, want_events, want_pre_merge) for _ in scans]
+        for attempt in range(2):
+            res = (frbx_results * len(scans))()
+            bufs_l, ser_l = [], []
+            for i, (n_bl, T, _) in enumerate(shapes):
+                bufs, r = _result_buffers(caps_l[i])
+                ser = None
+                if want_series:
+                    _, S_tot = frbx_series_layout(T, win)
+                    n = n_bl * len(dm) * S_tot
+                    ser = (np.zeros(n, SEG_DTYPE), np.zeros(n, np.float32), S_tot)
+                    r.series = ser[0].ctypes.data_as(c_vp)
+                    r.pnorm = ser[1].ctypes.data_as(c_vp)
+                    r.series_cap = n
+                res[i] = r
+                bufs_l.append(bufs)
+                ser_l.append(ser)
+            rc = lib.frbx_search_batch(self.b, arr, len(scans), _ptr(dm, c_f64), len(dm), _ptr(win, c_i32), len(win),
+                                       ctypes.byref(p), res, _stream_ptr(stream))
+            if rc == FRBX_ETRUNC and attempt == 0:
+                for i in range(len(scans)):
+                    for k in bufs_l[i]:
+                        if bufs_l[i][k].size:
+                            caps_l[i][k] = max(caps_l[i][k], int(getattr(res[i], k + "_count")))
+                continue
+            if rc != FRBX_OK:
+                raise FrbxError(rc, self.last_error())
+            break
+        outs = []
+        for i, (n_bl, T, _) in enumerate(shapes):
+            o = _collect(bufs_l[i], res[i])
+            if ser_l[i] is not None:
+                S_tot = ser_l[i][2]
+                o["S_tot"] = S_tot
+                o["series"] = ser_l[i][0].reshape(n_bl, len(dm), S_tot)
+                o["pnorm"] = ser_l[i][1].reshape(n_bl, len(dm), S_tot)
+            outs.append(o)
+        return outs
 
 
 # ------------------------------------------------------------------ refinement (autograd)

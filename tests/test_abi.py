@@ -41,7 +41,8 @@ def test_struct_layouts_match_header(frbx, tmp_path):
     ctypes and numpy layouts the binding uses."""
     structs = {"frbx_setup": frbx.frbx_setup, "frbx_params": frbx.frbx_params, "frbx_seg": frbx.frbx_seg,
                "frbx_event": frbx.frbx_event, "frbx_cand": frbx.frbx_cand, "frbx_group": frbx.frbx_group,
-               "frbx_results": frbx.frbx_results}
+               "frbx_results": frbx.frbx_results, "frbx_scan": frbx.frbx_scan,
+               "frbx_batch_stats": frbx.frbx_batch_stats}
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', 'int main(void){']
     for name, cls in structs.items():
         lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
