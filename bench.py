@@ -64,7 +64,10 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel", type=int, default=0)
-    ap.add_argument("--no-variants", action="store_true", help="skip the tensor-core BF16 variant")
+    ap.add_argument("--no-variants", action="store_true", help="skip the tensor-core and batched variants")
+    ap.add_argument("--batch-bl", type=int, default=3, help="baselines per scan of the batched variant")
+    ap.add_argument("--batch-scale", type=float, default=0.25, help="scan-length factor of the batched variant")
+    ap.add_argument("--batch-steps", type=int, default=2)
     return ap.parse_args()
 
 
@@ -90,6 +93,46 @@ def workload_config(name, wl):
                         f"({wl.n_chan} subbands x {wl.n_point}), windows {wl.windows}",
             "n_bl": wl.n_bl, "n_dm": int(len(wl.dms)), "T": wl.T, "n_point_total": wl.C,
             "windows": wl.windows, "l2_flush": "inputs larger than L2 (cube %.2f GB)" % (wl.n_bl * wl.T * wl.C * 8 / 1e9)}
+
+
+def run_batch_variant(frbx, torch, stream, n_bl, t_scale, steps, barrier):
+    """The batched search (many scans, uneven lengths, three setups) through frbx_search_batch:
+    one untimed call (time-tile tuning and graph capture), then `steps` timed calls that
+    replay the captured fit."""
+    wls = synth.make_batch(n_bl=n_bl, t_scale=t_scale)
+    handles, scans = {}, []
+    for wl in wls:
+        if wl.name not in handles:
+            handles[wl.name] = frbx.Handle.from_workload(wl)
+        scans.append((handles[wl.name], torch.from_numpy(synth.generate(wl)).cuda()))
+    dms, windows = wls[0].dms, wls[0].windows
+    cells = sum(float(wl.n_bl) * len(wl.dms) * wl.T * wl.C for wl in wls)
+    with frbx.Batch() as b:
+        b.search(scans, dms, windows, stream=stream)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fit, launches = [], 0
+        e0.record(stream)
+        for _ in range(steps):
+            outs = b.search(scans, dms, windows, stream=stream)
+            info = b.info()
+            fit.append(info["fit_ms"])
+            launches += info["launches"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+    kinds = {}
+    for wl in wls:
+        kinds[wl.name] = kinds.get(wl.name, 0) + 1
+    return {"value": cells / (ms / 1e3), "unit": "cells/s", "ms_per_step": ms, "steps": steps,
+            "fit_ms": statistics.mean(fit), "gpu_launches": launches,
+            "workload": f"{len(wls)} scans x {n_bl} baselines, T {min(w.T for w in wls)}..{max(w.T for w in wls)} APs "
+                        f"(1-30 s x {t_scale} at 1 ms), setups {kinds}, {len(dms)} DM trials 0..1500, "
+                        f"windows {windows}",
+            "cube_gb": sum(w.n_bl * w.T * w.C * 8 for w in wls) / 1e9, "cells": cells,
+            "time_tile": info["time_tile"], "graph_captures": info["graph_captures"],
+            "graph_replays": info["graph_replays"],
+            "pulses": int(sum(o["counts"]["pulses"] for o in outs)), "dtype": "f32"}
 
 
 def cells_of(wl):
@@ -369,6 +412,13 @@ def main():
             line_variants = {"tensor_bf16": {"unavailable": str(exc)}}
     else:
         line_variants = None
+    if not args.no_variants and args.kernel == 0:
+        try:
+            line_variants = line_variants or {}
+            line_variants["batch"] = run_batch_variant(frbx, torch, stream, args.batch_bl, args.batch_scale,
+                                                       max(1, args.batch_steps), barrier)
+        except Exception as exc:
+            line_variants["batch"] = {"unavailable": str(exc)}
     if line_variants:
         line["variants"] = line_variants
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -230,7 +230,7 @@ int frbx_create(const frbx_setup *s, frbx_handle **out) {
   };
   std::vector<float2> tws = tw(h->Ls), twm = tw(h->Lm);
   // FFT-kernel tables
-  std::vector<float2> sbd_tw, mbd_tw;
+  std::vector<float2> sbd_tw, mbd_tw, tree_tw;
   std::vector<int> slot;
   if (h->Ls % 32 == 0) {  // SBD four-step table (FFT and tensor-core fits)
     const int PS = h->Ls / 32, JP = h->J1 * 32;
@@ -254,6 +254,18 @@ int frbx_create(const frbx_setup *s, frbx_handle **out) {
     for (int g2 = 0; g2 < 32; ++g2)
       for (int o = 0; o < 4; ++o)
         h->slot_n[g2][o] = (short)(o < (int)res[(size_t)g2].size() ? res[(size_t)g2][(size_t)o] : -1);
+    // window-tree fit: half h of the 32-point DIF over residues g2 = g_n mod 32 takes channel n
+    // with exp(-2 pi i [(g_n q1 mod Lm) / Lm + h (g_n mod 32) / 32]) -- the MBD twiddle times
+    // the first-stage factor (+1, or -w32^(g mod 16) for the odd half), from the exact index
+    tree_tw.resize((size_t)N * PM * 2);
+    for (int n = 0; n < N; ++n)
+      for (int q1 = 0; q1 < PM; ++q1)
+        for (int hh = 0; hh < 2; ++hh) {
+          const long long g = h->g[(size_t)n];
+          const long long ex = ((g * q1) % h->Lm) * 32 + hh * (g % 32) * h->Lm;
+          const double th = two_pi * (double)(ex % (32LL * h->Lm)) / (32.0 * h->Lm);
+          tree_tw[((size_t)n * PM + q1) * 2 + hh] = make_float2((float)std::cos(th), (float)-std::sin(th));
+        }
   }
   // BF16 DFT matrix of the MBD transform for the tensor-core fit, in its shared-memory image
   // (rows: chunks of NC output columns, first half Re G, second half Im G; K-major, 64-wide
@@ -299,6 +311,7 @@ int frbx_create(const frbx_setup *s, frbx_handle **out) {
   if (e == cudaSuccess) e = upload(&h->d_sbd_tw, sbd_tw);
   if (e == cudaSuccess) e = upload(&h->d_mbd_tw, mbd_tw);
   if (e == cudaSuccess) e = upload(&h->d_slot, slot);
+  if (e == cudaSuccess) e = upload(&h->d_tree_tw, tree_tw);
   if (e == cudaSuccess && !bimg.empty()) e = upload((uint16_t **)&h->d_bimg, bimg);
   if (e == cudaSuccess) {
     std::call_once(g_const_once, frbx::set_fft_constants);
@@ -316,14 +329,15 @@ int frbx_create(const frbx_setup *s, frbx_handle **out) {
 
 void frbx_destroy(frbx_handle *h) {
   if (!h) return;
-  void *ptrs[] = {h->d_f, h->d_f0, h->d_wrot, h->d_tw_s, h->d_tw_m, h->d_g, h->d_sbd_tw, h->d_mbd_tw, h->d_slot, h->d_bimg};
+  void *ptrs[] = {h->d_f,      h->d_f0,     h->d_wrot, h->d_tw_s, h->d_tw_m,     h->d_g,
+                  h->d_sbd_tw, h->d_mbd_tw, h->d_slot, h->d_bimg, h->d_tree_tw};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : h->ev)
     if (e) cudaEventDestroy(e);
   frbx_handle::Buf *bufs[] = {&h->vis, &h->dk, &h->dk_max, &h->series, &h->pnorm, &h->stats,
                               &h->counts, &h->offsets, &h->events, &h->small, &h->seglist, &h->masks,
-                              &h->errflag, &h->refine, &h->calib};
+                              &h->errflag, &h->refine, &h->calib, &h->ytree};
   for (auto *b : bufs)
     if (b->p) cudaFree(b->p);
   delete h;
@@ -393,7 +407,7 @@ int check_params(frbx_handle *h, const frbx_params *p, int n_bl, FitArgs *a) {
   if (!axis_window(Lm, p->mbd_win_ns, [&](int s) { return ((double)s * 1000.0) / ((double)Lm * dfg); },
                    &a->q_lo, &a->q_len))
     return fail(h, FRBX_EINVAL, "MBD window holds no grid cell");
-  if (p->kernel < 0 || p->kernel > 3) return fail(h, FRBX_EINVAL, "kernel must be 0, 1, 2 or 3");
+  if (p->kernel < 0 || p->kernel > 4) return fail(h, FRBX_EINVAL, "kernel must be 0, 1, 2, 3 or 4");
   if (p->kernel == 3) {
     if (!h->d_bimg) return fail(h, FRBX_EUNSUPPORTED, "tensor-core fit needs Ls of 64 or 128, 2 Lm >= 32, N <= 64");
     if (a->m_len != Ls || a->q_len != Lm)
@@ -522,6 +536,75 @@ int run_stats(frbx_handle *h, StatsArgs sa, cudaStream_t st, std::vector<frbx_ev
 }
 
 }  // namespace
+
+// Multi-window fit through the matrix additivity of Sec. 5.1 (kernels_tree.cu): per chunk of
+// (baseline, DM) series, the SBD pass writes the transformed one-AP spectra, the MBD pass
+// builds every window from them and merges the maxima into the series buffer (as 64-bit
+// keys, zeroed first); a last pass turns the keys into frbx_seg records.  d_tab holds the
+// window tables and valid-segment counts in the layout frbx_search uploads.
+int run_fit_tree(frbx_handle *h, const FitArgs &a, const frbx_params &p, int nlev, const int32_t *windows, int n_win,
+                 const std::vector<int> &dkm, int n_bl, int T, int n_dm, const int *d_tab, int S_tot, cudaStream_t st) {
+  const size_t n_el = (size_t)n_bl * n_dm * S_tot;
+  if (n_el == 0) return FRBX_OK;
+  FRBX_CK(h, cudaMemsetAsync(a.out, 0, sizeof(frbx_seg) * n_el, st));
+  frbx::TreeArgs t{};
+  t.dk_max = (const int *)h->dk_max.p;
+  t.T = T;
+  t.keys = reinterpret_cast<unsigned long long *>(a.out);
+  t.n_dm = n_dm;
+  t.S_tot = S_tot;
+  t.win_off = d_tab + frbx::kMaxWin;
+  t.N = h->N;
+  t.Ls = h->Ls;
+  t.Lm = h->Lm;
+  t.PM = h->Lm / 32;
+  t.RB = 128 / (2 * t.PM);
+  t.n_mb = h->Ls / t.RB;
+  t.nlev = nlev;
+  for (int &e : t.emit_w) e = -1;
+  for (int w = 0; w < n_win; ++w) t.emit_w[__builtin_ctz((unsigned)windows[w])] = w;
+  t.m_lo = a.m_lo;
+  t.m_len = a.m_len;
+  t.q_lo = a.q_lo;
+  t.q_len = a.q_len;
+  t.tw = h->d_tree_tw;
+  std::memcpy(t.slot_n, h->slot_n, sizeof(t.slot_n));
+  t.TT = 1024;
+  t.n_tt = (T + t.TT - 1) / t.TT;
+  t.k_per_cta = 16;
+  t.n_ktile = (T + t.k_per_cta - 1) / t.k_per_cta;
+  t.y_series = (size_t)T * h->Ls * h->N;
+  const bool full = a.m_lo == 0 && a.m_len == h->Ls && a.q_lo == 0 && a.q_len == h->Lm;
+  // series whose dispersion sweep fits the scan, baseline-major
+  std::vector<int2> ser;
+  for (int b = 0; b < n_bl; ++b)
+    for (int d = 0; d < n_dm; ++d)
+      if (T - dkm[(size_t)d] >= 1) ser.push_back(make_int2(b, d));
+  if (!ser.empty()) {
+    size_t free_b = 0, total_b = 0;
+    FRBX_CK(h, cudaMemGetInfo(&free_b, &total_b));
+    const size_t per = sizeof(float2) * t.y_series;
+    const size_t budget = std::max(per, std::min<size_t>((size_t)8 << 30, (free_b + h->ytree.bytes) / 2));
+    const size_t chunk = std::max<size_t>(1, std::min(ser.size(), budget / per));
+    const size_t ser_bytes = (sizeof(int2) * ser.size() + 255) & ~(size_t)255;
+    FRBX_CK(h, ensure(h->ytree, ser_bytes + per * chunk));
+    int2 *d_ser = (int2 *)h->ytree.p;
+    FRBX_CK(h, cudaMemcpyAsync(d_ser, ser.data(), sizeof(int2) * ser.size(), cudaMemcpyHostToDevice, st));
+    t.Y = (float2 *)((char *)h->ytree.p + ser_bytes);
+    for (size_t c0 = 0; c0 < ser.size(); c0 += chunk) {
+      t.series = d_ser + c0;
+      t.n_s = (int)std::min(chunk, ser.size() - c0);
+      cudaError_t e = frbx::launch_tree_sbd(a, t, st, &h->launches);
+      if (e == cudaSuccess) e = frbx::launch_tree_mbd(t, h->occ, full, st, &h->launches);
+      if (e == cudaErrorInvalidConfiguration) return fail(h, FRBX_EUNSUPPORTED, "window-tree fit does not fit this shape");
+      FRBX_CK(h, e);
+    }
+  }
+  FRBX_CK(h, frbx::launch_tree_finalize(a.out, (long long)n_el, S_tot, n_dm, n_win, d_tab, d_tab + frbx::kMaxWin,
+                                         d_tab + 3 * frbx::kMaxWin, a.log2Lm, h->Lm, st, &h->launches));
+  (void)p;
+  return FRBX_OK;
+}
 
 // Everything after the fit (Eq. 6 and threshold on the device, then the host extraction of
 // Sec. 2.4.1 b-d, the DM merge of Sec. 5.3, cross-matching and the power sums of Sec. 2.4.2)
@@ -682,6 +765,7 @@ extern "C" int frbx_fit_segments(frbx_handle *h, const void *vis, int32_t vis_on
   FRBX_CK(h, ensure(h->seglist, sizeof(int32_t) * 4 * (size_t)n_seg));
   FRBX_CK(h, ensure(h->series, sizeof(frbx_seg) * (size_t)n_seg));
   FRBX_CK(h, cudaMemcpyAsync(h->seglist.p, segs, sizeof(int32_t) * 4 * (size_t)n_seg, cudaMemcpyHostToDevice, st));
+  if (p.kernel == 4) p.kernel = 0;  // explicit segment lists have no window structure to exploit
   fill_fit_tables(h, &a, dvis, T, n_dm);
   a.seg = (const int *)h->seglist.p;
   a.n_seg = n_seg;
@@ -773,7 +857,14 @@ extern "C" int frbx_search(frbx_handle *h, const void *vis, int32_t vis_on_devic
   a.TT = 64;
   a.out = (frbx_seg *)h->series.p;
   FRBX_CK(h, cudaEventRecord(h->ev[2], st));
-  if (p.kernel == 3) {
+  int nlev = 0;
+  const bool tree_ok = frbx::tree_supported(h->Ls, h->Lm, h->N, h->J, h->occ, windows, n_win, &nlev);
+  if (p.kernel == 4 && !tree_ok)
+    return fail(h, FRBX_EUNSUPPORTED, "window-tree fit needs power-of-two windows <= 64 and Ls, Lm multiples of 32");
+  if (p.kernel == 4 || (p.kernel == 0 && tree_ok)) {
+    rc = run_fit_tree(h, a, p, nlev, windows, n_win, dkm, n_bl, T, n_dm, d_tab, L.S_tot, st);
+    if (rc) return rc;
+  } else if (p.kernel == 3) {
     long long nv = 0;
     for (int v : L.n_valid) nv += v;
     rc = run_fit_mma(h, a, n_bl, false, nv * n_bl, st);

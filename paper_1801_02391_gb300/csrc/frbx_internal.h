@@ -129,6 +129,34 @@ cudaError_t launch_fit_fft_batch(const FitArgs &a, const BatchScan *scans_dev, i
 size_t max_smem_optin();
 bool fit_grid(const FitArgs &a, int n_bl, bool list_mode, dim3 *grid);
 
+// kernels_tree.cu: multi-window fit through the additivity of the delay-resolution matrix
+struct TreeArgs {
+  // chunk of (baseline, DM) series
+  const int2 *series;      // [n_s] (bl, d)
+  int n_s;
+  const int *dk_max;       // [n_dm]
+  int T;
+  float2 *Y;               // [n_s][T][Ls][N] SBD-transformed one-AP spectra
+  size_t y_series;         // float2 per series in Y
+  int n_ktile, k_per_cta;  // SBD pass: APs per CTA
+  // merged maxima, in the series buffer viewed as 64-bit keys [n_bl][n_dm][S_tot]
+  unsigned long long *keys;
+  int n_dm, S_tot;
+  const int *win_off;      // [n_win]
+  int N, Ls, Lm, PM, RB, n_mb, TT, n_tt, nlev;
+  int emit_w[8];           // window index of level e (window 2^e), -1 = not searched
+  int m_lo, m_len, q_lo, q_len;
+  const float2 *tw;        // [N][PM][2] MBD twiddles folded with the first DIF stage
+  short slot_n[32][4];
+};
+bool tree_supported(int Ls, int Lm, int N, int J, int occ, const int *windows, int n_win, int *nlev);
+cudaError_t launch_tree_sbd(const FitArgs &a, const TreeArgs &t, cudaStream_t st, int64_t *launches);
+cudaError_t launch_tree_mbd(const TreeArgs &t, int occ, bool full, cudaStream_t st, int64_t *launches);
+cudaError_t launch_tree_finalize(frbx_seg *series, long long n_el, int S_tot, int n_dm, int n_win, const int *win_len,
+                                 const int *win_off, const int *n_valid, int log2Lm, int Lm, cudaStream_t st,
+                                 int64_t *launches);
+void set_tree_constants();
+
 // kernels_misc.cu
 cudaError_t launch_shift_table(const double *f, int C, double fref, const double *dm, int n_dm,
                                double t_ap, int *dk, int *dk_max, cudaStream_t st,
@@ -191,6 +219,7 @@ struct frbx_handle {
   double *d_f = nullptr, *d_f0 = nullptr;
   float2 *d_wrot = nullptr, *d_tw_s = nullptr, *d_tw_m = nullptr;
   float2 *d_sbd_tw = nullptr, *d_mbd_tw = nullptr;
+  float2 *d_tree_tw = nullptr;  // [N][Lm/32][2] MBD twiddles of the window-tree fit
   void *d_bimg = nullptr;  // BF16 DFT matrix image for the tensor-core fit (if supported)
   int b_bytes = 0, b_atom_bytes = 0, KA = 0, NC = 0;
   int *d_g = nullptr, *d_slot = nullptr;
@@ -199,5 +228,6 @@ struct frbx_handle {
     void *p = nullptr;
     size_t bytes = 0;
   };
-  Buf vis, dk, dk_max, series, pnorm, stats, counts, offsets, events, small, seglist, masks, errflag, refine, calib;
+  Buf vis, dk, dk_max, series, pnorm, stats, counts, offsets, events, small, seglist, masks, errflag, refine, calib,
+      ytree;
 };

@@ -144,6 +144,7 @@ __global__ void __launch_bounds__(kFftThreads, 4)
 void set_fft_constants() {
   upload_w32();
   set_mma_constants();
+  set_tree_constants();
 }
 
 bool fft_supported(int Ls, int Lm, int J) { return Ls % 32 == 0 && Lm % 32 == 0 && J <= Ls; }

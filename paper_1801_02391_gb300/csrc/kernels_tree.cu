@@ -1,0 +1,346 @@
+// Multi-window segment fit through the additivity of the delay-resolution matrix (Sec. 5.1):
+//
+//   G_{k0, l1} + G_{k0 + l1, l2} = G_{k0, l1 + l2}
+//
+// With windows that are powers of two on the half-overlap grid (step l/2, step 1 for l = 1),
+// every segment of window 2l is the sum of two segments of window l:
+//
+//   G_{2l}(k0) = G_l(k0) + G_l(k0 + l),   k0 a multiple of step(2l) = l,
+//
+// so the 2-D transform (Eq. 5 on the Sec. 5.1 grid) runs once per AP -- on the one-AP
+// segment -- and every longer window is built by matrix additions; the Eq. 3 sums over time
+// move from the spectra to the delay-resolution matrices.  Two kernels per chunk of
+// (baseline, DM) series:
+//
+//  k_tree_sbd  gathers the dedispersed one-AP spectrum X(n, j) = w c S(n, j, k + dk(n, j)) and
+//              applies the SBD transform per channel (32-point register FFTs, as in the
+//              segment fit), writing Y[series][k][m][n] to device memory;
+//  k_tree_mbd  owns a block of RB SBD rows m of one series and a time tile.  A thread owns 16
+//              cells of one row: for MBD column class q1 (q = q1 + PM q2) and half h it folds
+//              the channels into the 16 inputs of the second half of a 32-point DIF FFT
+//              (even or odd q2), runs a 16-point register FFT and walks the cells through the
+//              window tree: the newest matrix of every level is summed with the anchor of that
+//              level (the previous segment needed as first half), emitted, and becomes the new
+//              anchor.  The level-1 anchor lives in registers, deeper ones in shared memory.
+//              Each emitted segment's maximum over the block's cells is reduced in the CTA and
+//              merged across blocks by a 64-bit atomicMax on (|G|^2 bits, ~cell index) in the
+//              series buffer, which k_tree_finalize turns into frbx_seg records.
+#include "fit_common.cuh"
+#include "fft32.cuh"
+
+namespace frbx {
+
+constexpr int kTreeThreads = 128;
+constexpr int kTreeMaxLev = 6;  // windows up to 64 APs
+
+__host__ __device__ inline size_t tree_smem_bytes(int N, int PM, int RB, int nlev) {
+  const size_t tw = sizeof(float2) * (size_t)N * PM * 2;
+  const size_t yb = sizeof(float2) * 2 * (size_t)RB * N;
+  const size_t an = sizeof(float2) * (size_t)(nlev > 1 ? nlev - 1 : 0) * 16 * kTreeThreads;
+  const size_t red = sizeof(uint2) * 2 * (kTreeMaxLev + 1) * (kTreeThreads / 32);
+  return tw + yb + an + red;
+}
+
+// ----------------------------------------------------------------------------- SBD pass
+__global__ void __launch_bounds__(kTreeThreads, 4)
+    k_tree_sbd(const __grid_constant__ FitArgs a, const __grid_constant__ TreeArgs t) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int N = a.N, Ls = a.Ls, PS = Ls >> 5, lps = __ffs(PS) - 1;
+  const int JP = a.J1 * 32, xs = JP + 1;
+  float2 *X = reinterpret_cast<float2 *>(smem);  // [N][xs]
+  float2 *stw = X + N * xs;                      // [PS][xs]
+  for (int i = threadIdx.x; i < N * xs; i += blockDim.x) X[i] = make_float2(0.f, 0.f);
+  for (int i = threadIdx.x; i < PS * JP; i += blockDim.x) {
+    const int r = i / JP, c = i - r * JP;
+    stw[r * xs + c] = a.sbd_tw[i];
+  }
+  const int tile = blockIdx.x % t.n_ktile, s = blockIdx.x / t.n_ktile;
+  const int2 sd = t.series[s];
+  const int kd = a.T - t.dk_max[sd.y];
+  const int k_lo = tile * t.k_per_cta, k_hi = min(kd, k_lo + t.k_per_cta);
+  const int *dk = a.dk + (size_t)sd.y * a.C;
+  float2 *Ys = t.Y + (size_t)s * t.y_series;
+  __syncthreads();
+  for (int k = k_lo; k < k_hi; ++k) {
+    // Eq. 3 with l = 1: the dedispersed spectrum of AP k, weighted and rotated
+    const size_t row0 = (size_t)sd.x * a.T + k;
+    for (int p = threadIdx.x; p < a.C; p += blockDim.x) {
+      const float2 v = __ldg(a.vis + (row0 + __ldg(dk + p)) * a.C + p);
+      const int n = p / a.J, j = p - n * a.J;
+      X[n * xs + j] = cmul(v, __ldg(a.wrot + p));
+    }
+    __syncthreads();
+    // SBD transform of every channel, task (n, m1); Y row m = m1 + PS m2 holds all channels
+    float2 *Yk = Ys + (size_t)k * Ls * N;
+    for (int u = threadIdx.x; u < N * PS; u += blockDim.x) {
+      const int n = u >> lps, m1 = u & (PS - 1);
+      float2 A[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) A[i] = make_float2(0.f, 0.f);
+      const float2 *xr = X + n * xs;
+      const float2 *wr = stw + m1 * xs;
+      for (int j1 = 0; j1 < a.J1; ++j1) {
+#pragma unroll
+        for (int j2 = 0; j2 < 32; ++j2) A[j2] = cfma(A[j2], xr[j1 * 32 + j2], wr[j1 * 32 + j2]);
+      }
+      fft32_dif(A);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) Yk[(size_t)(m1 + PS * bitrev5(i)) * N + n] = A[i];
+    }
+    __syncthreads();
+  }
+}
+
+// ----------------------------------------------------------------------------- MBD + tree
+// Packed per-thread key: |G|^2 with its 6 low mantissa bits replaced by 32 - q2 (a 2^-17
+// relative truncation, so equal truncated powers prefer the lower q2, i.e. the lower cell).
+__device__ __forceinline__ unsigned cell_key(float2 v, int q2) {
+  const float p = fmaf(v.x, v.x, v.y * v.y);
+  return (__float_as_uint(p) & ~63u) | (unsigned)(32 - q2);
+}
+
+template <int OCC, bool kFull>
+__global__ void __launch_bounds__(kTreeThreads, 3) k_tree_mbd(const __grid_constant__ TreeArgs t) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int N = t.N, PM = t.PM, RB = t.RB, Lm = t.Lm;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float2 *tw = reinterpret_cast<float2 *>(smem);  // [N][PM][2]
+  float2 *yb = tw + N * PM * 2;                    // [2][RB][N]
+  float2 *anc = yb + 2 * RB * N;                   // [nlev-1][16][128]
+  uint2 *red = reinterpret_cast<uint2 *>(anc + (t.nlev > 1 ? t.nlev - 1 : 0) * 16 * kTreeThreads);  // [2][7][4]
+
+  int item = blockIdx.x;
+  const int tt = item % t.n_tt;
+  item /= t.n_tt;
+  const int mb = item % t.n_mb, s = item / t.n_mb;
+  const int tpr = 2 * PM;
+  const int rr = tid / tpr, q1 = (tid >> 1) & (PM - 1), h = tid & 1;
+  const int m = mb * RB + rr;
+  const int2 sd = t.series[s];
+  const int kd = t.T - t.dk_max[sd.y];
+  const int kb = tt * t.TT;
+  if (kb >= kd) return;  // every segment starting here runs past the scan
+  bool row_in = true;
+  if (!kFull) {
+    row_in = ((m - t.m_lo) & (t.Ls - 1)) < t.m_len;
+    if (!__syncthreads_or(row_in)) return;  // no SBD row of this block is searched
+  }
+  const int lmax = 1 << t.nlev;
+  const int ke = min(kd, kb + t.TT + lmax - 1);
+
+  for (int i = tid; i < N * PM * 2; i += kTreeThreads) tw[i] = t.tw[i];
+  for (int i = tid; i < (t.nlev > 1 ? t.nlev - 1 : 0) * 16 * kTreeThreads; i += kTreeThreads)
+    anc[i] = make_float2(0.f, 0.f);
+  // cells this thread may report: c -> q2 = 2 bitrev4(c) + h, q = q1 + PM q2
+  unsigned cmask = 0xffffu;
+  if (!kFull) {
+    cmask = 0u;
+    if (row_in) {
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const int q2 = 2 * (bitrev5(c) >> 1) + h;
+        if ((((q1 + PM * q2) - t.q_lo) & (Lm - 1)) < t.q_len) cmask |= 1u << c;
+      }
+    }
+  }
+  const int rbn = RB * N;
+  const float2 *Ysrc = t.Y + (size_t)s * t.y_series + (size_t)mb * rbn;
+  const size_t ystep = (size_t)t.Ls * N;
+  for (int i = tid; i < rbn; i += kTreeThreads) yb[i] = __ldg(Ysrc + (size_t)kb * ystep + i);
+  unsigned long long *keys = t.keys + ((size_t)sd.x * t.n_dm + sd.y) * t.S_tot;
+  __syncthreads();
+
+  float2 a1[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) a1[c] = make_float2(0.f, 0.f);
+  const float2 *twp = tw + q1 * 2 + h;
+  const int twn = PM * 2;
+
+  for (int k = kb; k < ke; ++k) {
+    const int buf = (k - kb) & 1;
+    // next AP's rows into registers while this one is transformed (at most 4 per thread)
+    float2 nxt[4];
+    const bool more = k + 1 < ke;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = tid + u * kTreeThreads;
+      if (more && i < rbn) nxt[u] = __ldg(Ysrc + (size_t)(k + 1) * ystep + i);
+    }
+    // MBD: fold the channels into the 16 inputs of half h of the 32-point DIF FFT, then FFT16
+    const float2 *yr = yb + buf * rbn + rr * N;
+    float2 acc[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      acc[r] = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int o = 0; o < OCC; ++o) {
+        const int n0 = t.slot_n[r][o], n1 = t.slot_n[r + 16][o];
+        if (n0 >= 0) acc[r] = cfma(acc[r], yr[n0], twp[n0 * twn]);
+        if (n1 >= 0) acc[r] = cfma(acc[r], yr[n1], twp[n1 * twn]);
+      }
+    }
+    fft16_dif(acc);
+    // window tree: level e holds the segment of 2^e APs ending at AP k
+    const int ctz = __ffs(k + 1) - 1;
+    const int E = t.nlev == 0 ? 0 : min(t.nlev, ctz + 1);
+    for (int e = 0; e <= E; ++e) {
+      if (e == 1) {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const float2 g = acc[c];
+          acc[c] = make_float2(a1[c].x + g.x, a1[c].y + g.y);
+          a1[c] = g;
+        }
+      } else if (e >= 2) {
+        float2 *an = anc + (size_t)(e - 2) * 16 * kTreeThreads + tid;
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const float2 g = acc[c], p = an[c * kTreeThreads];
+          acc[c] = make_float2(p.x + g.x, p.y + g.y);
+          an[c * kTreeThreads] = g;
+        }
+      }
+      const int w = t.emit_w[e];
+      const int k0 = k - (1 << e) + 1;
+      if (w >= 0 && k0 >= kb && k0 < kb + t.TT) {  // uniform across the CTA
+        unsigned key = 0u;
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const unsigned kc = cell_key(acc[c], 2 * (bitrev5(c) >> 1) + h);
+          key = max(key, (cmask >> c) & 1u ? kc : 0u);
+        }
+        const unsigned wmax = __reduce_max_sync(0xffffffffu, key);
+        const unsigned win = __ballot_sync(0xffffffffu, key == wmax);
+        if (lane == 0) {
+          uint2 r2 = make_uint2(0u, 0xffffffffu);
+          if (wmax != 0u) {
+            const int L = __ffs(win) - 1, tl = warp * 32 + L;
+            const int q2 = 32 - (int)(wmax & 63u);
+            const int mm = mb * RB + tl / tpr, qq1 = (tl >> 1) & (PM - 1);
+            r2 = make_uint2(wmax & ~63u, (unsigned)(mm * Lm + qq1 + PM * q2));
+          }
+          red[(buf * (kTreeMaxLev + 1) + e) * 4 + warp] = r2;
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = tid + u * kTreeThreads;
+      if (more && i < rbn) yb[(buf ^ 1) * rbn + i] = nxt[u];
+    }
+    __syncthreads();
+    // merge the block's maxima of the segments emitted at AP k into the series
+    if (tid <= E) {
+      const int e = tid, w = t.emit_w[e], k0 = k - (1 << e) + 1;
+      if (w >= 0 && k0 >= kb && k0 < kb + t.TT) {
+        uint2 best = make_uint2(0u, 0xffffffffu);
+        for (int v = 0; v < kTreeThreads / 32; ++v) {
+          const uint2 r2 = red[(buf * (kTreeMaxLev + 1) + e) * 4 + v];
+          if (r2.x > best.x || (r2.x == best.x && r2.y < best.y)) best = r2;
+        }
+        if (best.x != 0u) {
+          const int l = 1 << e, step = l > 1 ? l / 2 : 1;
+          const unsigned long long kv = ((unsigned long long)best.x << 32) | (unsigned long long)(~best.y);
+          atomicMax(keys + t.win_off[w] + k0 / step, kv);
+        }
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------- finalize
+// Series element -> frbx_seg: valid slots decode the merged key, the others are empty (-1).
+__global__ void k_tree_finalize(frbx_seg *series, long long n_el, int S_tot, int n_dm, int n_win,
+                                const int *win_len, const int *win_off, const int *n_valid, int log2Lm, int Lm) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_el) return;
+  const int slot = (int)(i % S_tot);
+  const int d = (int)((i / S_tot) % n_dm);
+  int w = 0;
+  while (w + 1 < n_win && slot >= win_off[w + 1]) ++w;
+  const bool valid = slot - win_off[w] < n_valid[d * n_win + w];
+  unsigned long long *kp = reinterpret_cast<unsigned long long *>(series + i);
+  const unsigned long long key = *kp;
+  frbx_seg r;
+  if (valid && key != 0ull) {
+    const unsigned idx = ~(unsigned)(key & 0xffffffffull);
+    r.amp = sqrtf(__uint_as_float((unsigned)(key >> 32)));
+    r.sbd_idx = (uint16_t)(idx >> log2Lm);
+    r.mbd_idx = (uint16_t)(idx & (unsigned)(Lm - 1));
+  } else {
+    r.amp = -1.f;
+    r.sbd_idx = 0;
+    r.mbd_idx = 0;
+  }
+  series[i] = r;
+}
+
+// ----------------------------------------------------------------------------- host side
+void set_tree_constants() { upload_w32(); }
+
+bool tree_supported(int Ls, int Lm, int N, int J, int occ, const int *windows, int n_win, int *nlev) {
+  if (Ls % 32 != 0 || Lm % 32 != 0 || J > Ls || occ < 1 || occ > 4) return false;
+  const int PM = Lm / 32;
+  if (2 * PM > kTreeThreads) return false;
+  const int RB = kTreeThreads / (2 * PM);
+  if (Ls % RB != 0 || RB * N > 4 * kTreeThreads) return false;
+  int lmax = 1;
+  for (int w = 0; w < n_win; ++w) {
+    const int l = windows[w];
+    if (l < 1 || (l & (l - 1)) != 0 || l > (1 << kTreeMaxLev)) return false;
+    lmax = std::max(lmax, l);
+  }
+  *nlev = __builtin_ctz((unsigned)lmax);
+  return tree_smem_bytes(N, PM, RB, *nlev) <= max_smem_optin();
+}
+
+size_t tree_sbd_smem(const FitArgs &a) {
+  const int JP = a.J1 * 32;
+  return sizeof(float2) * ((size_t)a.N * (JP + 1) + (size_t)(a.Ls / 32) * (JP + 1));
+}
+
+cudaError_t launch_tree_sbd(const FitArgs &a, const TreeArgs &t, cudaStream_t st, int64_t *launches) {
+  const size_t smem = tree_sbd_smem(a);
+  if (smem > max_smem_optin()) return cudaErrorInvalidConfiguration;
+  const long long nb = (long long)t.n_s * t.n_ktile;
+  if (nb <= 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_tree_sbd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_tree_sbd<<<(unsigned)nb, kTreeThreads, smem, st>>>(a, t);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+template <int OCC, bool kFull>
+static cudaError_t launch_mbd_one(const TreeArgs &t, unsigned nb, size_t smem, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(k_tree_mbd<OCC, kFull>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_tree_mbd<OCC, kFull><<<nb, kTreeThreads, smem, st>>>(t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tree_mbd(const TreeArgs &t, int occ, bool full, cudaStream_t st, int64_t *launches) {
+  const size_t smem = tree_smem_bytes(t.N, t.PM, t.RB, t.nlev);
+  if (smem > max_smem_optin()) return cudaErrorInvalidConfiguration;
+  const long long nb = (long long)t.n_s * t.n_mb * t.n_tt;
+  if (nb <= 0) return cudaSuccess;
+  if (nb > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  cudaError_t e;
+  if (occ == 1) e = full ? launch_mbd_one<1, true>(t, (unsigned)nb, smem, st) : launch_mbd_one<1, false>(t, (unsigned)nb, smem, st);
+  else if (occ == 2) e = full ? launch_mbd_one<2, true>(t, (unsigned)nb, smem, st) : launch_mbd_one<2, false>(t, (unsigned)nb, smem, st);
+  else e = full ? launch_mbd_one<4, true>(t, (unsigned)nb, smem, st) : launch_mbd_one<4, false>(t, (unsigned)nb, smem, st);
+  ++*launches;
+  return e;
+}
+
+cudaError_t launch_tree_finalize(frbx_seg *series, long long n_el, int S_tot, int n_dm, int n_win, const int *win_len,
+                                 const int *win_off, const int *n_valid, int log2Lm, int Lm, cudaStream_t st,
+                                 int64_t *launches) {
+  if (n_el <= 0) return cudaSuccess;
+  k_tree_finalize<<<(unsigned)((n_el + 255) / 256), 256, 0, st>>>(series, n_el, S_tot, n_dm, n_win, win_len, win_off,
+                                                                   n_valid, log2Lm, Lm);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+}  // namespace frbx

@@ -21,6 +21,11 @@ available; these stand in for it with the paper's shapes):
   3.0 and 10.7 GHz (the VGOS setup of Sec. 4), 0.5 ms APs, T = 20000,
   512 DM trials 0..2000, five pulses, 5 % of the points flagged and carrying
   RFI.
+* ``batch``  -- many scans for the batched search: 16 scans of uneven length
+  (1-30 s at 1 ms APs), 45 baselines (10 stations), each scan on one of three
+  setups (256 points: the small layout; 1024 points: the two lower VGOS bands;
+  2048 points: all four VGOS bands), 256 DM trials 0..1500, a pulse in a quarter
+  of the scans.
 """
 from __future__ import annotations
 
@@ -207,3 +212,47 @@ def pure_tone_segment(wl: Workload, tau_ns: float, amp: float = 1.0) -> np.ndarr
     """Noise-free [N*J] spectrum a*exp(2 pi i (f - f0[0]) tau) for transform pins."""
     f = wl.point_freqs()
     return (amp * np.exp(2j * math.pi * (f - wl.f0_mhz[0]) * tau_ns * 1e-3)).astype(np.complex128)
+
+
+BATCH_SETUPS = ("c256", "c1024", "c2048")
+
+
+def _batch_setup(kind: str, wid: int, T: int, n_bl: int, dms) -> Workload:
+    if kind == "c256":
+        f0, J = 1400.0 + 32.0 * np.arange(8), 32
+    else:
+        bands = [3000.0, 5464.0] if kind == "c1024" else [3000.0, 5464.0, 7960.0, 10424.0]
+        f0, J = np.array([b + 32.0 * i for b in bands for i in range(8)]), 64
+    wl = Workload(name=kind, workload_id=wid, n_bl=n_bl, f0_mhz=f0, n_point=J, f_bw_mhz=32.0, t_ap_ms=1.0, T=T,
+                  dms=np.asarray(dms, np.float64), windows=[2, 4, 8, 16])
+    if kind != "c256":  # the VGOS-like setups carry 5 % flagged points; one flag set per setup
+        fr = np.random.Generator(np.random.PCG64(seed_for(30 + BATCH_SETUPS.index(kind), "flags")))
+        wl.flags = (fr.random(wl.C) < 0.05).astype(np.uint8)
+        wl.rfi_points = [(int(c // J), int(c % J)) for c in np.flatnonzero(wl.flags)]
+    else:
+        fr = np.random.Generator(np.random.PCG64(seed_for(30, "rfi")))
+        wl.rfi_points = [(int(fr.integers(0, 8)), int(fr.integers(1, J))) for _ in range(2)]
+    return wl
+
+
+def make_batch(n_scans: int = 16, n_bl: int = 45, n_dm: int = 256, t_scale: float = 1.0,
+               seed_offset: int = 0) -> list:
+    """The batched-search workload: a list of Workloads, one per scan (``name`` is the
+    scan's setup, so scans with equal names share one setup)."""
+    rng = np.random.Generator(np.random.PCG64(seed_for(20 + seed_offset, "geometry")))
+    dms = np.linspace(0.0, 1500.0, n_dm)
+    kinds = [BATCH_SETUPS[int(k)] for k in rng.integers(0, 3, n_scans)]
+    lengths = [max(64, int(round(rng.uniform(1.0, 30.0) * 1000.0 * t_scale))) for _ in range(n_scans)]
+    with_pulse = set(int(i) for i in rng.choice(n_scans, max(1, n_scans // 4), replace=False))
+    out = []
+    for s in range(n_scans):
+        wl = _batch_setup(kinds[s], 100 + 20 * seed_offset + s, lengths[s], n_bl, dms)
+        wl.tau_g_ns = rng.uniform(1.0, 50.0, n_bl)
+        wl.rate_mhz = rng.uniform(-5.0, 5.0, n_bl)
+        wl.phase0 = rng.uniform(0.0, 2 * math.pi, n_bl)
+        if s in with_pulse:
+            T = lengths[s]
+            wl.pulses = [Pulse(dm=float(rng.uniform(100.0, 1400.0)), t0_bin=int(rng.integers(0, max(1, T // 2))),
+                               width=int(rng.integers(1, 11)), snr=float(rng.uniform(8.0, 30.0)))]
+        out.append(wl)
+    return out

@@ -1,0 +1,130 @@
+"""Window-tree fit (kernel 4, the automatic choice where it applies): every window of a
+power-of-two set is built from one-AP delay-resolution matrices by the additivity of
+Sec. 5.1, G_{k0,l} + G_{k0+l,l} = G_{k0,2l}.  Compared with the FP64 oracle element by
+element, on several grid shapes (Lm/32 = 16, 8 and 1 MBD column classes), window sets with
+and without gaps, more than one time tile, delay windows and scans that DM trials sweep past."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import reference as R
+from tests.gpu_helpers import assert_fit_match
+from tests.test_gpu_parity import compare_search
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def frbx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1801_02391_gb300 import _build
+    _build.build()
+    from paper_1801_02391_gb300 import frbx as f
+    f.load()
+    return f
+
+
+def to_dev(vis):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(vis)).cuda()
+
+
+def _vgos(T=1300, n_bl=2, dms=(0.0, 100.0, 400.0, 1700.0)):
+    wl = synth.make_vgos(T=T, n_bl=n_bl, n_dm=len(dms))
+    wl.dms = np.array(dms)
+    for p in wl.pulses:
+        p.t0_bin = int(p.t0_bin % 200 + 50)
+        p.dm = float(wl.dms[min(2, len(dms) - 1)])
+    return wl
+
+
+def _run(frbx, wl, windows, combos=(3,), kernel=4, **kw):
+    wl.windows = list(windows)
+    st = R.setup_from_workload(wl)
+    vis = synth.generate(wl)
+    res_o = R.search(st, vis, wl.dms, wl.windows, combos=list(combos))
+    h = frbx.Handle.from_workload(wl)
+    out = h.search(to_dev(vis), wl.dms, wl.windows, combos=list(combos), want_series=True, want_events=True,
+                   want_pre_merge=True, kernel=kernel, **kw)
+    compare_search(frbx, wl, st, vis, res_o, out, list(combos))
+    return h, out
+
+
+@pytest.mark.parametrize("windows", [[1, 2, 4, 8, 16, 32], [2, 4, 8, 16], [1, 4, 16], [8], [64, 1]])
+def test_tree_search_matches_oracle(frbx, windows):
+    # T = 1300 spans two time tiles of 1024 APs; DM 1700 leaves about 400 APs of valid sweep
+    _run(frbx, _vgos(), windows)
+
+
+def test_tree_is_the_automatic_choice(frbx):
+    wl = _vgos(T=700, n_bl=2, dms=(0.0, 400.0))
+    wl.windows = [1, 2, 4, 8]
+    vis = to_dev(synth.generate(wl))
+    h = frbx.Handle.from_workload(wl)
+    auto = h.search(vis, wl.dms, wl.windows, want_series=True)
+    tree = h.search(vis, wl.dms, wl.windows, want_series=True, kernel=4)
+    assert np.array_equal(auto["series"], tree["series"])
+    seg = h.search(vis, wl.dms, wl.windows, want_series=True, kernel=2)
+    ok = seg["series"]["amp"] >= 0
+    assert np.array_equal(ok, tree["series"]["amp"] >= 0)
+    np.testing.assert_allclose(tree["series"]["amp"][ok], seg["series"]["amp"][ok], rtol=1e-4)
+
+
+def test_tree_two_band_grid(frbx):
+    """Two VGOS bands (16 x 64 points): Lm = 256, eight SBD rows per block."""
+    wl = synth._batch_setup("c1024", 41, 1100, 2, [0.0, 300.0, 900.0])
+    wl.tau_g_ns = np.array([12.0, 31.0])
+    wl.rate_mhz = np.array([1.0, -2.0])
+    wl.phase0 = np.array([0.3, 2.0])
+    wl.pulses = [synth.Pulse(dm=300.0, t0_bin=200, width=3, snr=25.0)]
+    _run(frbx, wl, [2, 4, 8, 16], combos=(3, 1))
+
+
+def test_tree_single_column_class_grid(frbx):
+    """4 channels x 32 points with channel offsets {0, 3, 7, 12} x 16 MHz: Lm = 32, so one MBD
+    column class and all 64 SBD rows in one block."""
+    wl = synth.make_tiny(n_chan=4, n_point=32, T=400, n_bl=2, dms=(0.0, 50.0, 200.0), windows=(1, 2, 4, 8),
+                         f0=800.0 + 16.0 * np.array([0, 3, 7, 12]))
+    h, _ = _run(frbx, wl, [1, 2, 4, 8])
+    assert (h.Ls, h.Lm) == (64, 32)
+
+
+def test_tree_delay_windows(frbx):
+    """SBD / MBD search windows: blocks of SBD rows outside the window are skipped, cells
+    outside it are excluded from the maximum."""
+    wl = _vgos(T=600, n_bl=2, dms=(0.0, 400.0))
+    wl.windows = [1, 2, 4, 8]
+    st = R.setup_from_workload(wl)
+    vis = synth.generate(wl)
+    sbd, mbd = (-100.0, 150.0), (-2.0, 3.0)
+    h = frbx.Handle.from_workload(wl)
+    out = h.search(to_dev(vis), wl.dms, wl.windows, want_series=True, kernel=4, sbd_win_ns=sbd, mbd_win_ns=mbd)
+    dk = R.shift_table(st, wl.dms)
+    segs, idx, _ = R.all_segments(wl.T, wl.n_bl, wl.windows, dk.max(axis=1))
+    am, aq = R.window_masks(st, sbd, mbd)
+    ref = R.fit_segments(st, vis, dk, segs, am, aq)
+    flat = out["series"].reshape(-1)[idx]
+    assert (flat["amp"] >= 0).all()
+    assert_fit_match(st, vis, dk, segs, flat, ref, (am, aq))
+    m = flat["sbd_idx"].astype(int)
+    assert am[m].all() and aq[flat["mbd_idx"].astype(int)].all()
+
+
+def test_tree_scan_swept_past(frbx):
+    """DM trials whose sweep exceeds the scan have no valid segment; the rest are fitted."""
+    wl = _vgos(T=300, n_bl=1, dms=(0.0, 2000.0))
+    h, out = _run(frbx, wl, [1, 2, 4], combos=(1,))
+    assert np.all(out["series"]["amp"][0, 1] == -1.0) and np.all(out["series"]["amp"][0, 0] >= 0)
+
+
+def test_tree_rejects_other_windows(frbx):
+    wl = _vgos(T=300, n_bl=1, dms=(0.0,))
+    h = frbx.Handle.from_workload(wl)
+    with pytest.raises(frbx.FrbxError) as e:
+        h.search(to_dev(synth.generate(wl)), wl.dms, [3, 6], kernel=4)
+    assert e.value.code == frbx.FRBX_EUNSUPPORTED
+    # the automatic choice falls back to the per-segment fit for such windows
+    out = h.search(to_dev(synth.generate(wl)), wl.dms, [3, 6], want_series=True)
+    assert (out["series"]["amp"] >= 0).any()
