@@ -231,7 +231,7 @@ int frbx_create(const frbx_setup *s, frbx_handle **out) {
   std::vector<float2> tws = tw(h->Ls), twm = tw(h->Lm);
   // FFT-kernel tables
   std::vector<float2> sbd_tw, mbd_tw, tree_tw;
-  std::vector<int> slot;
+  std::vector<int> slot, tree_slot;
   if (h->Ls % 32 == 0) {  // SBD four-step table (FFT and tensor-core fits)
     const int PS = h->Ls / 32, JP = h->J1 * 32;
     sbd_tw.assign((size_t)PS * JP, make_float2(0.f, 0.f));
@@ -254,17 +254,27 @@ int frbx_create(const frbx_setup *s, frbx_handle **out) {
     for (int g2 = 0; g2 < 32; ++g2)
       for (int o = 0; o < 4; ++o)
         h->slot_n[g2][o] = (short)(o < (int)res[(size_t)g2].size() ? res[(size_t)g2][(size_t)o] : -1);
-    // window-tree fit: half h of the 32-point DIF over residues g2 = g_n mod 32 takes channel n
-    // with exp(-2 pi i [(g_n q1 mod Lm) / Lm + h (g_n mod 32) / 32]) -- the MBD twiddle times
-    // the first-stage factor (+1, or -w32^(g mod 16) for the odd half), from the exact index
-    tree_tw.resize((size_t)N * PM * 2);
+    // window-tree fit: channel n sits in slot (g_n mod 16) + 16 o of a Y row (o its rank in
+    // the class); half h of the 32-point DIF over residues g2 = g_n mod 32 takes it with
+    // exp(-2 pi i [(g_n q1 mod Lm) / Lm + h (g_n mod 32) / 32]) -- the MBD twiddle times the
+    // first-stage factor (+1, or -w32^(g mod 16) for the odd half), from the exact index
+    std::vector<int> cnt16(16, 0);
+    tree_slot.resize((size_t)N);
+    for (int n = 0; n < N; ++n) {
+      const int r = (int)(h->g[(size_t)n] % 16);
+      tree_slot[(size_t)n] = r + 16 * cnt16[(size_t)r]++;
+    }
+    h->tree_s16 = *std::max_element(cnt16.begin(), cnt16.end());
+    const int NS = 16 * h->tree_s16;
+    tree_tw.assign((size_t)NS * PM * 2, make_float2(0.f, 0.f));
     for (int n = 0; n < N; ++n)
       for (int q1 = 0; q1 < PM; ++q1)
         for (int hh = 0; hh < 2; ++hh) {
           const long long g = h->g[(size_t)n];
           const long long ex = ((g * q1) % h->Lm) * 32 + hh * (g % 32) * h->Lm;
           const double th = two_pi * (double)(ex % (32LL * h->Lm)) / (32.0 * h->Lm);
-          tree_tw[((size_t)n * PM + q1) * 2 + hh] = make_float2((float)std::cos(th), (float)-std::sin(th));
+          tree_tw[((size_t)tree_slot[(size_t)n] * PM + q1) * 2 + hh] =
+              make_float2((float)std::cos(th), (float)-std::sin(th));
         }
   }
   // BF16 DFT matrix of the MBD transform for the tensor-core fit, in its shared-memory image
@@ -312,6 +322,7 @@ int frbx_create(const frbx_setup *s, frbx_handle **out) {
   if (e == cudaSuccess) e = upload(&h->d_mbd_tw, mbd_tw);
   if (e == cudaSuccess) e = upload(&h->d_slot, slot);
   if (e == cudaSuccess) e = upload(&h->d_tree_tw, tree_tw);
+  if (e == cudaSuccess) e = upload(&h->d_tree_slot, tree_slot);
   if (e == cudaSuccess && !bimg.empty()) e = upload((uint16_t **)&h->d_bimg, bimg);
   if (e == cudaSuccess) {
     std::call_once(g_const_once, frbx::set_fft_constants);
@@ -330,7 +341,7 @@ int frbx_create(const frbx_setup *s, frbx_handle **out) {
 void frbx_destroy(frbx_handle *h) {
   if (!h) return;
   void *ptrs[] = {h->d_f,      h->d_f0,     h->d_wrot, h->d_tw_s, h->d_tw_m,     h->d_g,
-                  h->d_sbd_tw, h->d_mbd_tw, h->d_slot, h->d_bimg, h->d_tree_tw};
+                  h->d_sbd_tw, h->d_mbd_tw, h->d_slot, h->d_bimg, h->d_tree_tw, h->d_tree_slot};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : h->ev)
@@ -555,6 +566,8 @@ int run_fit_tree(frbx_handle *h, const FitArgs &a, const frbx_params &p, int nle
   t.S_tot = S_tot;
   t.win_off = d_tab + frbx::kMaxWin;
   t.N = h->N;
+  t.NS = 16 * h->tree_s16;
+  t.slot_of = h->d_tree_slot;
   t.Ls = h->Ls;
   t.Lm = h->Lm;
   t.PM = h->Lm / 32;
@@ -568,12 +581,11 @@ int run_fit_tree(frbx_handle *h, const FitArgs &a, const frbx_params &p, int nle
   t.q_lo = a.q_lo;
   t.q_len = a.q_len;
   t.tw = h->d_tree_tw;
-  std::memcpy(t.slot_n, h->slot_n, sizeof(t.slot_n));
   t.TT = 1024;
   t.n_tt = (T + t.TT - 1) / t.TT;
   t.k_per_cta = 16;
   t.n_ktile = (T + t.k_per_cta - 1) / t.k_per_cta;
-  t.y_series = (size_t)T * h->Ls * h->N;
+  t.y_series = (size_t)T * h->Ls * t.NS;
   const bool full = a.m_lo == 0 && a.m_len == h->Ls && a.q_lo == 0 && a.q_len == h->Lm;
   // series whose dispersion sweep fits the scan, baseline-major
   std::vector<int2> ser;
@@ -583,19 +595,23 @@ int run_fit_tree(frbx_handle *h, const FitArgs &a, const frbx_params &p, int nle
   if (!ser.empty()) {
     size_t free_b = 0, total_b = 0;
     FRBX_CK(h, cudaMemGetInfo(&free_b, &total_b));
-    const size_t per = sizeof(float2) * t.y_series;
+    // per series: its transformed spectra and the deep anchors of its MBD CTAs
+    const size_t anc_per = sizeof(float2) * frbx::tree_anchor_floats(nlev) * t.n_mb * t.n_tt;
+    const size_t per = sizeof(float2) * t.y_series + anc_per;
     const size_t budget = std::max(per, std::min<size_t>((size_t)8 << 30, (free_b + h->ytree.bytes) / 2));
     const size_t chunk = std::max<size_t>(1, std::min(ser.size(), budget / per));
     const size_t ser_bytes = (sizeof(int2) * ser.size() + 255) & ~(size_t)255;
-    FRBX_CK(h, ensure(h->ytree, ser_bytes + per * chunk));
+    const size_t y_bytes = (sizeof(float2) * t.y_series * chunk + 255) & ~(size_t)255;
+    FRBX_CK(h, ensure(h->ytree, ser_bytes + y_bytes + anc_per * chunk));
     int2 *d_ser = (int2 *)h->ytree.p;
     FRBX_CK(h, cudaMemcpyAsync(d_ser, ser.data(), sizeof(int2) * ser.size(), cudaMemcpyHostToDevice, st));
     t.Y = (float2 *)((char *)h->ytree.p + ser_bytes);
+    t.anc_g = (float2 *)((char *)h->ytree.p + ser_bytes + y_bytes);
     for (size_t c0 = 0; c0 < ser.size(); c0 += chunk) {
       t.series = d_ser + c0;
       t.n_s = (int)std::min(chunk, ser.size() - c0);
       cudaError_t e = frbx::launch_tree_sbd(a, t, st, &h->launches);
-      if (e == cudaSuccess) e = frbx::launch_tree_mbd(t, h->occ, full, st, &h->launches);
+      if (e == cudaSuccess) e = frbx::launch_tree_mbd(t, full, st, &h->launches);
       if (e == cudaErrorInvalidConfiguration) return fail(h, FRBX_EUNSUPPORTED, "window-tree fit does not fit this shape");
       FRBX_CK(h, e);
     }
@@ -858,7 +874,7 @@ extern "C" int frbx_search(frbx_handle *h, const void *vis, int32_t vis_on_devic
   a.out = (frbx_seg *)h->series.p;
   FRBX_CK(h, cudaEventRecord(h->ev[2], st));
   int nlev = 0;
-  const bool tree_ok = frbx::tree_supported(h->Ls, h->Lm, h->N, h->J, h->occ, windows, n_win, &nlev);
+  const bool tree_ok = frbx::tree_supported(h->Ls, h->Lm, h->N, h->J, h->tree_s16, windows, n_win, &nlev);
   if (p.kernel == 4 && !tree_ok)
     return fail(h, FRBX_EUNSUPPORTED, "window-tree fit needs power-of-two windows <= 64 and Ls, Lm multiples of 32");
   if (p.kernel == 4 || (p.kernel == 0 && tree_ok)) {

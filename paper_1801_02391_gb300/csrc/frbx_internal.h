@@ -143,15 +143,17 @@ struct TreeArgs {
   unsigned long long *keys;
   int n_dm, S_tot;
   const int *win_off;      // [n_win]
-  int N, Ls, Lm, PM, RB, n_mb, TT, n_tt, nlev;
+  int N, NS, Ls, Lm, PM, RB, n_mb, TT, n_tt, nlev;
   int emit_w[8];           // window index of level e (window 2^e), -1 = not searched
   int m_lo, m_len, q_lo, q_len;
-  const float2 *tw;        // [N][PM][2] MBD twiddles folded with the first DIF stage
-  short slot_n[32][4];
+  const int *slot_of;      // [N] slot of channel n in a Y row: (g_n mod 16) + 16 rank
+  const float2 *tw;        // [NS][PM][2] MBD twiddles folded with the first DIF stage (0: empty)
+  float2 *anc_g;           // deep window-tree anchors, one slice per MBD CTA
 };
-bool tree_supported(int Ls, int Lm, int N, int J, int occ, const int *windows, int n_win, int *nlev);
+bool tree_supported(int Ls, int Lm, int N, int J, int s16, const int *windows, int n_win, int *nlev);
+size_t tree_anchor_floats(int nlev);  // float2 per MBD CTA in TreeArgs::anc_g
 cudaError_t launch_tree_sbd(const FitArgs &a, const TreeArgs &t, cudaStream_t st, int64_t *launches);
-cudaError_t launch_tree_mbd(const TreeArgs &t, int occ, bool full, cudaStream_t st, int64_t *launches);
+cudaError_t launch_tree_mbd(const TreeArgs &t, bool full, cudaStream_t st, int64_t *launches);
 cudaError_t launch_tree_finalize(frbx_seg *series, long long n_el, int S_tot, int n_dm, int n_win, const int *win_len,
                                  const int *win_off, const int *n_valid, int log2Lm, int Lm, cudaStream_t st,
                                  int64_t *launches);
@@ -219,7 +221,9 @@ struct frbx_handle {
   double *d_f = nullptr, *d_f0 = nullptr;
   float2 *d_wrot = nullptr, *d_tw_s = nullptr, *d_tw_m = nullptr;
   float2 *d_sbd_tw = nullptr, *d_mbd_tw = nullptr;
-  float2 *d_tree_tw = nullptr;  // [N][Lm/32][2] MBD twiddles of the window-tree fit
+  float2 *d_tree_tw = nullptr;  // [16 s16][Lm/32][2] MBD twiddles of the window-tree fit
+  int *d_tree_slot = nullptr;   // [N] channel slot of the window-tree fit
+  int tree_s16 = 0;             // slots per residue class mod 16 (0: no window-tree fit)
   void *d_bimg = nullptr;  // BF16 DFT matrix image for the tensor-core fit (if supported)
   int b_bytes = 0, b_atom_bytes = 0, KA = 0, NC = 0;
   int *d_g = nullptr, *d_slot = nullptr;

@@ -14,14 +14,16 @@
 //
 //  k_tree_sbd  gathers the dedispersed one-AP spectrum X(n, j) = w c S(n, j, k + dk(n, j)) and
 //              applies the SBD transform per channel (32-point register FFTs, as in the
-//              segment fit), writing Y[series][k][m][n] to device memory;
+//              segment fit), writing Y[series][k][m][slot] to device memory, where channel n
+//              sits in slot (g_n mod 16) + 16 o (o its rank in that class, empty slots zero);
 //  k_tree_mbd  owns a block of RB SBD rows m of one series and a time tile.  A thread owns 16
 //              cells of one row: for MBD column class q1 (q = q1 + PM q2) and half h it folds
-//              the channels into the 16 inputs of the second half of a 32-point DIF FFT
-//              (even or odd q2), runs a 16-point register FFT and walks the cells through the
-//              window tree: the newest matrix of every level is summed with the anchor of that
-//              level (the previous segment needed as first half), emitted, and becomes the new
-//              anchor.  The level-1 anchor lives in registers, deeper ones in shared memory.
+//              the channel slots (a static loop) into the 16 inputs of one half of a 32-point
+//              DIF FFT (even or odd q2), runs a 16-point register FFT and walks the cells
+//              through the window tree: the newest matrix of every level is summed with the
+//              anchor of that level (the previous segment needed as first half), emitted, and
+//              becomes the new anchor.  The level-1 anchor lives in registers, the next three in
+//              shared memory, deeper ones in an L2-resident per-CTA slice of device memory.
 //              Each emitted segment's maximum over the block's cells is reduced in the CTA and
 //              merged across blocks by a 64-bit atomicMax on (|G|^2 bits, ~cell index) in the
 //              series buffer, which k_tree_finalize turns into frbx_seg records.
@@ -33,22 +35,31 @@ namespace frbx {
 constexpr int kTreeThreads = 128;
 constexpr int kTreeMaxLev = 6;  // windows up to 64 APs
 
-__host__ __device__ inline size_t tree_smem_bytes(int N, int PM, int RB, int nlev) {
-  const size_t tw = sizeof(float2) * (size_t)N * PM * 2;
-  const size_t yb = sizeof(float2) * 2 * (size_t)RB * N;
-  const size_t an = sizeof(float2) * (size_t)(nlev > 1 ? nlev - 1 : 0) * 16 * kTreeThreads;
+// Anchors of the window tree: level 1 in registers, the next kTreeSmemAnc levels in shared
+// memory, deeper ones (touched every 16 APs or less often) in a per-CTA slice of device memory.
+constexpr int kTreeSmemAnc = 3;
+
+__host__ __device__ inline int tree_smem_anchors(int nlev) { return nlev - 1 < kTreeSmemAnc ? (nlev > 1 ? nlev - 1 : 0) : kTreeSmemAnc; }
+__host__ __device__ inline int tree_global_anchors(int nlev) { return (nlev > 1 ? nlev - 1 : 0) - tree_smem_anchors(nlev); }
+
+__host__ __device__ inline size_t tree_smem_bytes(int NS, int PM, int RB, int nlev) {
+  const size_t tw = sizeof(float2) * (size_t)NS * PM * 2;
+  const size_t yb = sizeof(float2) * 2 * (size_t)RB * NS;
+  const size_t an = sizeof(float2) * (size_t)tree_smem_anchors(nlev) * 16 * kTreeThreads;
   const size_t red = sizeof(uint2) * 2 * (kTreeMaxLev + 1) * (kTreeThreads / 32);
   return tw + yb + an + red;
 }
 
 // ----------------------------------------------------------------------------- SBD pass
-__global__ void __launch_bounds__(kTreeThreads, 4)
+__global__ void __launch_bounds__(kTreeThreads, 3)
     k_tree_sbd(const __grid_constant__ FitArgs a, const __grid_constant__ TreeArgs t) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int N = a.N, Ls = a.Ls, PS = Ls >> 5, lps = __ffs(PS) - 1;
+  const int N = a.N, Ls = a.Ls, PS = Ls >> 5, lps = __ffs(PS) - 1, NS = t.NS;
   const int JP = a.J1 * 32, xs = JP + 1;
-  float2 *X = reinterpret_cast<float2 *>(smem);  // [N][xs]
-  float2 *stw = X + N * xs;                      // [PS][xs]
+  float2 *Ys = reinterpret_cast<float2 *>(smem);  // [Ls][NS], channel slots in MBD fold order
+  float2 *X = Ys + Ls * NS;                       // [N][xs]
+  float2 *stw = X + N * xs;                       // [PS][xs]
+  for (int i = threadIdx.x; i < Ls * NS; i += blockDim.x) Ys[i] = make_float2(0.f, 0.f);  // empty slots stay 0
   for (int i = threadIdx.x; i < N * xs; i += blockDim.x) X[i] = make_float2(0.f, 0.f);
   for (int i = threadIdx.x; i < PS * JP; i += blockDim.x) {
     const int r = i / JP, c = i - r * JP;
@@ -59,7 +70,8 @@ __global__ void __launch_bounds__(kTreeThreads, 4)
   const int kd = a.T - t.dk_max[sd.y];
   const int k_lo = tile * t.k_per_cta, k_hi = min(kd, k_lo + t.k_per_cta);
   const int *dk = a.dk + (size_t)sd.y * a.C;
-  float2 *Ys = t.Y + (size_t)s * t.y_series;
+  float4 *Yout = reinterpret_cast<float4 *>(t.Y + (size_t)s * t.y_series);
+  const int row4 = Ls * NS / 2;  // float4 per AP
   __syncthreads();
   for (int k = k_lo; k < k_hi; ++k) {
     // Eq. 3 with l = 1: the dedispersed spectrum of AP k, weighted and rotated
@@ -70,8 +82,7 @@ __global__ void __launch_bounds__(kTreeThreads, 4)
       X[n * xs + j] = cmul(v, __ldg(a.wrot + p));
     }
     __syncthreads();
-    // SBD transform of every channel, task (n, m1); Y row m = m1 + PS m2 holds all channels
-    float2 *Yk = Ys + (size_t)k * Ls * N;
+    // SBD transform of every channel, task (n, m1); row m = m1 + PS m2 holds the channel slots
     for (int u = threadIdx.x; u < N * PS; u += blockDim.x) {
       const int n = u >> lps, m1 = u & (PS - 1);
       float2 A[32];
@@ -84,14 +95,29 @@ __global__ void __launch_bounds__(kTreeThreads, 4)
         for (int j2 = 0; j2 < 32; ++j2) A[j2] = cfma(A[j2], xr[j1 * 32 + j2], wr[j1 * 32 + j2]);
       }
       fft32_dif(A);
+      const int sl = __ldg(t.slot_of + n);
 #pragma unroll
-      for (int i = 0; i < 32; ++i) Yk[(size_t)(m1 + PS * bitrev5(i)) * N + n] = A[i];
+      for (int i = 0; i < 32; ++i) Ys[(m1 + PS * bitrev5(i)) * NS + sl] = A[i];
     }
+    __syncthreads();
+    const float4 *src = reinterpret_cast<const float4 *>(Ys);
+    float4 *dst = Yout + (size_t)k * row4;
+    for (int i = threadIdx.x; i < row4; i += blockDim.x) dst[i] = src[i];
     __syncthreads();
   }
 }
 
 // ----------------------------------------------------------------------------- MBD + tree
+// 16-byte global -> shared copy that bypasses the registers (completes at cp_async_wait).
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
 // Packed per-thread key: |G|^2 with its 6 low mantissa bits replaced by 32 - q2 (a 2^-17
 // relative truncation, so equal truncated powers prefer the lower q2, i.e. the lower cell).
 __device__ __forceinline__ unsigned cell_key(float2 v, int q2) {
@@ -99,15 +125,18 @@ __device__ __forceinline__ unsigned cell_key(float2 v, int q2) {
   return (__float_as_uint(p) & ~63u) | (unsigned)(32 - q2);
 }
 
-template <int OCC, bool kFull>
+template <int S16, bool kFull>
 __global__ void __launch_bounds__(kTreeThreads, 3) k_tree_mbd(const __grid_constant__ TreeArgs t) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int N = t.N, PM = t.PM, RB = t.RB, Lm = t.Lm;
+  constexpr int NS = 16 * S16;
+  const int PM = t.PM, RB = t.RB, Lm = t.Lm;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  float2 *tw = reinterpret_cast<float2 *>(smem);  // [N][PM][2]
-  float2 *yb = tw + N * PM * 2;                    // [2][RB][N]
-  float2 *anc = yb + 2 * RB * N;                   // [nlev-1][16][128]
-  uint2 *red = reinterpret_cast<uint2 *>(anc + (t.nlev > 1 ? t.nlev - 1 : 0) * 16 * kTreeThreads);  // [2][7][4]
+  const int n_sm = tree_smem_anchors(t.nlev);
+  float2 *tw = reinterpret_cast<float2 *>(smem);  // [NS][PM][2]
+  float2 *yb = tw + NS * PM * 2;                   // [2][RB][NS]
+  float2 *anc = yb + 2 * RB * NS;                  // [n_sm][16][128]
+  uint2 *red = reinterpret_cast<uint2 *>(anc + n_sm * 16 * kTreeThreads);  // [2][7][4]
+  float2 *ancg = t.anc_g + (size_t)blockIdx.x * tree_global_anchors(t.nlev) * 16 * kTreeThreads;
 
   int item = blockIdx.x;
   const int tt = item % t.n_tt;
@@ -128,9 +157,10 @@ __global__ void __launch_bounds__(kTreeThreads, 3) k_tree_mbd(const __grid_const
   const int lmax = 1 << t.nlev;
   const int ke = min(kd, kb + t.TT + lmax - 1);
 
-  for (int i = tid; i < N * PM * 2; i += kTreeThreads) tw[i] = t.tw[i];
-  for (int i = tid; i < (t.nlev > 1 ? t.nlev - 1 : 0) * 16 * kTreeThreads; i += kTreeThreads)
-    anc[i] = make_float2(0.f, 0.f);
+  for (int i = tid; i < NS * PM * 2; i += kTreeThreads) tw[i] = t.tw[i];
+  for (int i = tid; i < n_sm * 16 * kTreeThreads; i += kTreeThreads) anc[i] = make_float2(0.f, 0.f);
+  for (int i = tid; i < tree_global_anchors(t.nlev) * 16 * kTreeThreads; i += kTreeThreads)
+    ancg[i] = make_float2(0.f, 0.f);
   // cells this thread may report: c -> q2 = 2 bitrev4(c) + h, q = q1 + PM q2
   unsigned cmask = 0xffffu;
   if (!kFull) {
@@ -143,10 +173,12 @@ __global__ void __launch_bounds__(kTreeThreads, 3) k_tree_mbd(const __grid_const
       }
     }
   }
-  const int rbn = RB * N;
+  const int rbn = RB * NS, rb4 = rbn / 2;  // the block's rows of one AP, in float2 / float4
   const float2 *Ysrc = t.Y + (size_t)s * t.y_series + (size_t)mb * rbn;
-  const size_t ystep = (size_t)t.Ls * N;
-  for (int i = tid; i < rbn; i += kTreeThreads) yb[i] = __ldg(Ysrc + (size_t)kb * ystep + i);
+  const size_t ystep = (size_t)t.Ls * NS;
+  for (int i = tid; i < rb4; i += kTreeThreads)
+    cp_async16(reinterpret_cast<float4 *>(yb) + i, reinterpret_cast<const float4 *>(Ysrc + (size_t)kb * ystep) + i);
+  cp_async_wait();
   unsigned long long *keys = t.keys + ((size_t)sd.x * t.n_dm + sd.y) * t.S_tot;
   __syncthreads();
 
@@ -158,32 +190,29 @@ __global__ void __launch_bounds__(kTreeThreads, 3) k_tree_mbd(const __grid_const
 
   for (int k = kb; k < ke; ++k) {
     const int buf = (k - kb) & 1;
-    // next AP's rows into registers while this one is transformed (at most 4 per thread)
-    float2 nxt[4];
-    const bool more = k + 1 < ke;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int i = tid + u * kTreeThreads;
-      if (more && i < rbn) nxt[u] = __ldg(Ysrc + (size_t)(k + 1) * ystep + i);
+    // next AP's rows into the other buffer while this one is transformed
+    if (k + 1 < ke) {
+      float4 *dst = reinterpret_cast<float4 *>(yb + (buf ^ 1) * rbn);
+      const float4 *src = reinterpret_cast<const float4 *>(Ysrc + (size_t)(k + 1) * ystep);
+      for (int i = tid; i < rb4; i += kTreeThreads) cp_async16(dst + i, src + i);
     }
-    // MBD: fold the channels into the 16 inputs of half h of the 32-point DIF FFT, then FFT16
-    const float2 *yr = yb + buf * rbn + rr * N;
+    // MBD: the channels of slot (r, o) = r + 16 o fold into input r of half h of the 32-point
+    // DIF FFT (empty slots hold zeros), then a 16-point FFT
+    const float2 *yr = yb + buf * rbn + rr * NS;
     float2 acc[16];
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
       acc[r] = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int o = 0; o < OCC; ++o) {
-        const int n0 = t.slot_n[r][o], n1 = t.slot_n[r + 16][o];
-        if (n0 >= 0) acc[r] = cfma(acc[r], yr[n0], twp[n0 * twn]);
-        if (n1 >= 0) acc[r] = cfma(acc[r], yr[n1], twp[n1 * twn]);
-      }
+      for (int o = 0; o < S16; ++o) acc[r] = cfma(acc[r], yr[r + 16 * o], twp[(r + 16 * o) * twn]);
     }
     fft16_dif(acc);
     // window tree: level e holds the segment of 2^e APs ending at AP k
     const int ctz = __ffs(k + 1) - 1;
     const int E = t.nlev == 0 ? 0 : min(t.nlev, ctz + 1);
-    for (int e = 0; e <= E; ++e) {
+#pragma unroll
+    for (int e = 0; e <= kTreeMaxLev; ++e) {
+      if (e > E) break;
       if (e == 1) {
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
@@ -192,7 +221,8 @@ __global__ void __launch_bounds__(kTreeThreads, 3) k_tree_mbd(const __grid_const
           a1[c] = g;
         }
       } else if (e >= 2) {
-        float2 *an = anc + (size_t)(e - 2) * 16 * kTreeThreads + tid;
+        float2 *an = e - 2 < n_sm ? anc + (e - 2) * 16 * kTreeThreads + tid
+                                  : ancg + (e - 2 - n_sm) * 16 * kTreeThreads + tid;
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
           const float2 g = acc[c], p = an[c * kTreeThreads];
@@ -223,11 +253,7 @@ __global__ void __launch_bounds__(kTreeThreads, 3) k_tree_mbd(const __grid_const
         }
       }
     }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int i = tid + u * kTreeThreads;
-      if (more && i < rbn) yb[(buf ^ 1) * rbn + i] = nxt[u];
-    }
+    cp_async_wait();
     __syncthreads();
     // merge the block's maxima of the segments emitted at AP k into the series
     if (tid <= E) {
@@ -278,12 +304,12 @@ __global__ void k_tree_finalize(frbx_seg *series, long long n_el, int S_tot, int
 // ----------------------------------------------------------------------------- host side
 void set_tree_constants() { upload_w32(); }
 
-bool tree_supported(int Ls, int Lm, int N, int J, int occ, const int *windows, int n_win, int *nlev) {
-  if (Ls % 32 != 0 || Lm % 32 != 0 || J > Ls || occ < 1 || occ > 4) return false;
-  const int PM = Lm / 32;
-  if (2 * PM > kTreeThreads) return false;
+bool tree_supported(int Ls, int Lm, int N, int J, int s16, const int *windows, int n_win, int *nlev) {
+  if (Ls % 32 != 0 || Lm % 32 != 0 || J > Ls || s16 < 1 || s16 > 4) return false;
+  const int PM = Lm / 32, NS = 16 * s16;
+  if (2 * PM > kTreeThreads || N > NS) return false;
   const int RB = kTreeThreads / (2 * PM);
-  if (Ls % RB != 0 || RB * N > 4 * kTreeThreads) return false;
+  if (Ls % RB != 0) return false;
   int lmax = 1;
   for (int w = 0; w < n_win; ++w) {
     const int l = windows[w];
@@ -291,16 +317,18 @@ bool tree_supported(int Ls, int Lm, int N, int J, int occ, const int *windows, i
     lmax = std::max(lmax, l);
   }
   *nlev = __builtin_ctz((unsigned)lmax);
-  return tree_smem_bytes(N, PM, RB, *nlev) <= max_smem_optin();
+  return tree_smem_bytes(NS, PM, RB, *nlev) <= max_smem_optin();
 }
 
-size_t tree_sbd_smem(const FitArgs &a) {
+size_t tree_anchor_floats(int nlev) { return (size_t)tree_global_anchors(nlev) * 16 * kTreeThreads; }
+
+size_t tree_sbd_smem(const FitArgs &a, int NS) {
   const int JP = a.J1 * 32;
-  return sizeof(float2) * ((size_t)a.N * (JP + 1) + (size_t)(a.Ls / 32) * (JP + 1));
+  return sizeof(float2) * ((size_t)a.Ls * NS + (size_t)a.N * (JP + 1) + (size_t)(a.Ls / 32) * (JP + 1));
 }
 
 cudaError_t launch_tree_sbd(const FitArgs &a, const TreeArgs &t, cudaStream_t st, int64_t *launches) {
-  const size_t smem = tree_sbd_smem(a);
+  const size_t smem = tree_sbd_smem(a, t.NS);
   if (smem > max_smem_optin()) return cudaErrorInvalidConfiguration;
   const long long nb = (long long)t.n_s * t.n_ktile;
   if (nb <= 0) return cudaSuccess;
@@ -311,24 +339,29 @@ cudaError_t launch_tree_sbd(const FitArgs &a, const TreeArgs &t, cudaStream_t st
   return cudaGetLastError();
 }
 
-template <int OCC, bool kFull>
+template <int S16, bool kFull>
 static cudaError_t launch_mbd_one(const TreeArgs &t, unsigned nb, size_t smem, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(k_tree_mbd<OCC, kFull>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_tree_mbd<S16, kFull>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_tree_mbd<OCC, kFull><<<nb, kTreeThreads, smem, st>>>(t);
+  k_tree_mbd<S16, kFull><<<nb, kTreeThreads, smem, st>>>(t);
   return cudaGetLastError();
 }
 
-cudaError_t launch_tree_mbd(const TreeArgs &t, int occ, bool full, cudaStream_t st, int64_t *launches) {
-  const size_t smem = tree_smem_bytes(t.N, t.PM, t.RB, t.nlev);
+cudaError_t launch_tree_mbd(const TreeArgs &t, bool full, cudaStream_t st, int64_t *launches) {
+  const size_t smem = tree_smem_bytes(t.NS, t.PM, t.RB, t.nlev);
   if (smem > max_smem_optin()) return cudaErrorInvalidConfiguration;
   const long long nb = (long long)t.n_s * t.n_mb * t.n_tt;
   if (nb <= 0) return cudaSuccess;
   if (nb > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  const unsigned g = (unsigned)nb;
   cudaError_t e;
-  if (occ == 1) e = full ? launch_mbd_one<1, true>(t, (unsigned)nb, smem, st) : launch_mbd_one<1, false>(t, (unsigned)nb, smem, st);
-  else if (occ == 2) e = full ? launch_mbd_one<2, true>(t, (unsigned)nb, smem, st) : launch_mbd_one<2, false>(t, (unsigned)nb, smem, st);
-  else e = full ? launch_mbd_one<4, true>(t, (unsigned)nb, smem, st) : launch_mbd_one<4, false>(t, (unsigned)nb, smem, st);
+  switch (t.NS / 16) {
+    case 1: e = full ? launch_mbd_one<1, true>(t, g, smem, st) : launch_mbd_one<1, false>(t, g, smem, st); break;
+    case 2: e = full ? launch_mbd_one<2, true>(t, g, smem, st) : launch_mbd_one<2, false>(t, g, smem, st); break;
+    case 3: e = full ? launch_mbd_one<3, true>(t, g, smem, st) : launch_mbd_one<3, false>(t, g, smem, st); break;
+    case 4: e = full ? launch_mbd_one<4, true>(t, g, smem, st) : launch_mbd_one<4, false>(t, g, smem, st); break;
+    default: return cudaErrorInvalidConfiguration;
+  }
   ++*launches;
   return e;
 }
