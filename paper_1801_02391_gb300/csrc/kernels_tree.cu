@@ -182,13 +182,12 @@ __global__ void __launch_bounds__(kTreeThreads, 3) k_tree_mbd(const __grid_const
   unsigned long long *keys = t.keys + ((size_t)sd.x * t.n_dm + sd.y) * t.S_tot;
   __syncthreads();
 
-  float2 a1[16];
-#pragma unroll
-  for (int c = 0; c < 16; ++c) a1[c] = make_float2(0.f, 0.f);
   const float2 *twp = tw + q1 * 2 + h;
   const int twn = PM * 2;
 
-  for (int k = kb; k < ke; ++k) {
+  // One AP: cur receives the one-AP matrix G_1(k) of the thread's cells; prev holds G_1(k - 1)
+  // (the level-1 anchor).  Callers alternate the two arrays, so no anchor copy is needed.
+  auto ap = [&](const int k, const float2(&prev)[16], float2(&cur)[16]) {
     const int buf = (k - kb) & 1;
     // next AP's rows into the other buffer while this one is transformed
     if (k + 1 < ke) {
@@ -199,30 +198,31 @@ __global__ void __launch_bounds__(kTreeThreads, 3) k_tree_mbd(const __grid_const
     // MBD: the channels of slot (r, o) = r + 16 o fold into input r of half h of the 32-point
     // DIF FFT (empty slots hold zeros), then a 16-point FFT
     const float2 *yr = yb + buf * rbn + rr * NS;
-    float2 acc[16];
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
-      acc[r] = make_float2(0.f, 0.f);
+      float2 z = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int o = 0; o < S16; ++o) acc[r] = cfma(acc[r], yr[r + 16 * o], twp[(r + 16 * o) * twn]);
+      for (int o = 0; o < S16; ++o) z = cfma(z, yr[r + 16 * o], twp[(r + 16 * o) * twn]);
+      cur[r] = z;
     }
-    fft16_dif(acc);
+    fft16_dif(cur);
     // window tree: level e holds the segment of 2^e APs ending at AP k
     const int ctz = __ffs(k + 1) - 1;
     const int E = t.nlev == 0 ? 0 : min(t.nlev, ctz + 1);
+    float2 acc[16];
 #pragma unroll
     for (int e = 0; e <= kTreeMaxLev; ++e) {
       if (e > E) break;
-      if (e == 1) {
+      if (e == 0) {
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const float2 g = acc[c];
-          acc[c] = make_float2(a1[c].x + g.x, a1[c].y + g.y);
-          a1[c] = g;
-        }
-      } else if (e >= 2) {
-        float2 *an = e - 2 < n_sm ? anc + (e - 2) * 16 * kTreeThreads + tid
-                                  : ancg + (e - 2 - n_sm) * 16 * kTreeThreads + tid;
+        for (int c = 0; c < 16; ++c) acc[c] = cur[c];
+      } else if (e == 1) {
+#pragma unroll
+        for (int c = 0; c < 16; ++c) acc[c] = make_float2(prev[c].x + cur[c].x, prev[c].y + cur[c].y);
+      } else {
+        // anchors of levels 1..3 in shared memory, deeper ones in the CTA's device slice
+        float2 *an = e - 2 < kTreeSmemAnc ? anc + (e - 2) * 16 * kTreeThreads + tid
+                                          : ancg + (e - 2 - kTreeSmemAnc) * 16 * kTreeThreads + tid;
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
           const float2 g = acc[c], p = an[c * kTreeThreads];
@@ -271,7 +271,17 @@ __global__ void __launch_bounds__(kTreeThreads, 3) k_tree_mbd(const __grid_const
         }
       }
     }
+  };
+
+  float2 ga[16], gb[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) ga[c] = make_float2(0.f, 0.f);
+  int k = kb;
+  for (; k + 1 < ke; k += 2) {
+    ap(k, ga, gb);
+    ap(k + 1, gb, ga);
   }
+  if (k < ke) ap(k, ga, gb);
 }
 
 // ----------------------------------------------------------------------------- finalize
