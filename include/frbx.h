@@ -294,8 +294,13 @@ int frbx_extract_events(const frbx_event *events, int64_t n_events, int32_t n_se
  *  [0] shift table (Eq. 1-2)        [1] segment fit kernel (Eq. 3, Eq. 5, Sec. 5.1)
  *  [2] baselines: Eq. 6 + threshold  [3] combinations: sum + Eq. 6 + threshold
  *  [4] host extraction (Sec. 2.4.1 b-d, Sec. 5.3 merge, cross-matching, Sec. 2.4.2)
+ *  [5] window-tree fit: device time of its SBD-pass kernels, summed over its chunks
+ *  [6] window-tree fit: device time of its MBD-pass kernels (k_tree_mbd), summed
+ *  [7] window-tree fit: number of chunks (= launches of each of the two kernels)
  *  ms_out  [n] out, milliseconds (stages that did not run report 0).
- * Returns the number of stages written (min(n, 5)) or FRBX_EINVAL.
+ * Stages [5] and [6] are bracketed by events on the library's own chunk streams; chunks on
+ * the two streams overlap, so [5] + [6] can exceed [1].
+ * Returns the number of values written (min(n, 8)) or FRBX_EINVAL.
  */
 int frbx_last_stage_times(const frbx_handle *h, double *ms_out, int32_t n);
 

@@ -346,6 +346,12 @@ void frbx_destroy(frbx_handle *h) {
     if (p) cudaFree(p);
   for (cudaEvent_t e : h->ev)
     if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->tree_ev)
+    if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->tree_kev)
+    if (e) cudaEventDestroy(e);
+  for (cudaStream_t x : h->tree_st)
+    if (x) cudaStreamDestroy(x);
   frbx_handle::Buf *bufs[] = {&h->vis, &h->dk, &h->dk_max, &h->series, &h->pnorm, &h->stats,
                               &h->counts, &h->offsets, &h->events, &h->small, &h->seglist, &h->masks,
                               &h->errflag, &h->refine, &h->calib, &h->ytree};
@@ -585,7 +591,7 @@ int run_fit_tree(frbx_handle *h, const FitArgs &a, const frbx_params &p, int nle
   t.n_tt = (T + t.TT - 1) / t.TT;
   t.k_per_cta = 16;
   t.n_ktile = (T + t.k_per_cta - 1) / t.k_per_cta;
-  t.y_series = (size_t)T * h->Ls * t.NS;
+  t.y_series = (size_t)T * h->Ls * h->N;
   const bool full = a.m_lo == 0 && a.m_len == h->Ls && a.q_lo == 0 && a.q_len == h->Lm;
   // series whose dispersion sweep fits the scan, baseline-major
   std::vector<int2> ser;
@@ -595,25 +601,53 @@ int run_fit_tree(frbx_handle *h, const FitArgs &a, const frbx_params &p, int nle
   if (!ser.empty()) {
     size_t free_b = 0, total_b = 0;
     FRBX_CK(h, cudaMemGetInfo(&free_b, &total_b));
-    // per series: its transformed spectra and the deep anchors of its MBD CTAs
+    // per series: its transformed spectra and the deep anchors of its MBD CTAs.  Chunks
+    // alternate between two streams, each with its own spectra and anchor buffers, so the SBD
+    // pass of one chunk and the tail of the other chunk's MBD pass overlap.
     const size_t anc_per = sizeof(float2) * frbx::tree_anchor_floats(nlev) * t.n_mb * t.n_tt;
     const size_t per = sizeof(float2) * t.y_series + anc_per;
-    const size_t budget = std::max(per, std::min<size_t>((size_t)8 << 30, (free_b + h->ytree.bytes) / 2));
+    const size_t budget = std::max(per, std::min<size_t>((size_t)8 << 30, (free_b + h->ytree.bytes) / 4));
     const size_t chunk = std::max<size_t>(1, std::min(ser.size(), budget / per));
     const size_t ser_bytes = (sizeof(int2) * ser.size() + 255) & ~(size_t)255;
     const size_t y_bytes = (sizeof(float2) * t.y_series * chunk + 255) & ~(size_t)255;
-    FRBX_CK(h, ensure(h->ytree, ser_bytes + y_bytes + anc_per * chunk));
+    const size_t a_bytes = (anc_per * chunk + 255) & ~(size_t)255;
+    FRBX_CK(h, ensure(h->ytree, ser_bytes + 2 * (y_bytes + a_bytes)));
     int2 *d_ser = (int2 *)h->ytree.p;
     FRBX_CK(h, cudaMemcpyAsync(d_ser, ser.data(), sizeof(int2) * ser.size(), cudaMemcpyHostToDevice, st));
-    t.Y = (float2 *)((char *)h->ytree.p + ser_bytes);
-    t.anc_g = (float2 *)((char *)h->ytree.p + ser_bytes + y_bytes);
-    for (size_t c0 = 0; c0 < ser.size(); c0 += chunk) {
-      t.series = d_ser + c0;
-      t.n_s = (int)std::min(chunk, ser.size() - c0);
-      cudaError_t e = frbx::launch_tree_sbd(a, t, st, &h->launches);
-      if (e == cudaSuccess) e = frbx::launch_tree_mbd(t, full, st, &h->launches);
+    for (int i = 0; i < 2; ++i) {
+      if (!h->tree_st[i]) FRBX_CK(h, cudaStreamCreateWithFlags(&h->tree_st[i], cudaStreamNonBlocking));
+      if (!h->tree_ev[i]) FRBX_CK(h, cudaEventCreateWithFlags(&h->tree_ev[i], cudaEventDisableTiming));
+    }
+    if (!h->tree_ev[2]) FRBX_CK(h, cudaEventCreateWithFlags(&h->tree_ev[2], cudaEventDisableTiming));
+    FRBX_CK(h, cudaEventRecord(h->tree_ev[2], st));
+    for (int i = 0; i < 2; ++i) FRBX_CK(h, cudaStreamWaitEvent(h->tree_st[i], h->tree_ev[2], 0));
+    const int n_chunks = (int)((ser.size() + chunk - 1) / chunk);
+    while ((int)h->tree_kev.size() < 3 * n_chunks) {
+      cudaEvent_t ev = nullptr;
+      FRBX_CK(h, cudaEventCreate(&ev));
+      h->tree_kev.push_back(ev);
+    }
+    h->tree_chunks = n_chunks;
+    int par = 0, ci = 0;
+    for (size_t c0 = 0; c0 < ser.size(); c0 += chunk, par ^= 1, ++ci) {
+      frbx::TreeArgs tc = t;
+      char *base = (char *)h->ytree.p + ser_bytes + (size_t)par * (y_bytes + a_bytes);
+      tc.Y = (float2 *)base;
+      tc.anc_g = (float2 *)(base + y_bytes);
+      tc.series = d_ser + c0;
+      tc.n_s = (int)std::min(chunk, ser.size() - c0);
+      cudaEvent_t *kev = h->tree_kev.data() + 3 * ci;
+      cudaError_t e = cudaEventRecord(kev[0], h->tree_st[par]);
+      if (e == cudaSuccess) e = frbx::launch_tree_sbd(a, tc, h->tree_st[par], &h->launches);
+      if (e == cudaSuccess) e = cudaEventRecord(kev[1], h->tree_st[par]);
+      if (e == cudaSuccess) e = frbx::launch_tree_mbd(tc, full, h->tree_st[par], &h->launches);
+      if (e == cudaSuccess) e = cudaEventRecord(kev[2], h->tree_st[par]);
       if (e == cudaErrorInvalidConfiguration) return fail(h, FRBX_EUNSUPPORTED, "window-tree fit does not fit this shape");
       FRBX_CK(h, e);
+    }
+    for (int i = 0; i < 2; ++i) {
+      FRBX_CK(h, cudaEventRecord(h->tree_ev[i], h->tree_st[i]));
+      FRBX_CK(h, cudaStreamWaitEvent(st, h->tree_ev[i], 0));
     }
   }
   FRBX_CK(h, frbx::launch_tree_finalize(a.out, (long long)n_el, S_tot, n_dm, n_win, d_tab, d_tab + frbx::kMaxWin,
@@ -678,6 +712,16 @@ int finish_search(frbx_handle *h, const frbx_seg *series, int n_bl, int T, const
       FRBX_CK(h, cudaEventElapsedTime(&ms, h->ev[pairs[k][0]], h->ev[pairs[k][1]]));
       h->stage_ms[k] = ms;
     }
+    // window-tree fit: device time of its SBD and MBD kernels, summed over the chunks
+    h->stage_ms[5] = h->stage_ms[6] = h->stage_ms[7] = 0.0;
+    for (int c = 0; c < h->tree_chunks; ++c) {
+      const cudaEvent_t *kev = h->tree_kev.data() + 3 * c;
+      FRBX_CK(h, cudaEventElapsedTime(&ms, kev[0], kev[1]));
+      h->stage_ms[5] += ms;
+      FRBX_CK(h, cudaEventElapsedTime(&ms, kev[1], kev[2]));
+      h->stage_ms[6] += ms;
+    }
+    h->stage_ms[7] = h->tree_chunks;
   }
   const auto host_t0 = std::chrono::steady_clock::now();
 
@@ -822,6 +866,7 @@ extern "C" int frbx_search(frbx_handle *h, const void *vis, int32_t vis_on_devic
   int rc = check_params(h, &p, n_bl, &a);
   if (rc) return rc;
   for (double &v : h->stage_ms) v = 0.0;
+  h->tree_chunks = 0;
   for (cudaEvent_t &ev : h->ev)
     if (!ev) FRBX_CK(h, cudaEventCreate(&ev));
   const float2 *dvis = nullptr;
@@ -962,7 +1007,7 @@ extern "C" int frbx_extract_events(const frbx_event *events, int64_t n_events, i
 
 extern "C" int frbx_last_stage_times(const frbx_handle *h, double *ms_out, int32_t n) {
   if (!h || !ms_out || n < 0) return FRBX_EINVAL;
-  const int k = std::min(n, 5);
+  const int k = std::min(n, 8);
   for (int i = 0; i < k; ++i) ms_out[i] = h->stage_ms[i];
   return k;
 }
@@ -1447,6 +1492,7 @@ extern "C" int frbx_search_batch(frbx_batch *b, const frbx_scan *scans, int32_t 
     t2.insert(t2.end(), L.n_valid.begin(), L.n_valid.end());
     h->err.clear();
     h->launches = 0;
+    h->tree_chunks = 0;
     int rc = FRBX_OK;
     if (ensure(h->small, sizeof(int) * t2.size() + 4096) != cudaSuccess ||
         cudaMemcpyAsync(h->small.p, t2.data(), sizeof(int) * t2.size(), cudaMemcpyHostToDevice, st) != cudaSuccess) {

@@ -216,7 +216,7 @@ struct frbx_handle {
   std::string err;
   int64_t launches = 0;
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  double stage_ms[5] = {0, 0, 0, 0, 0};
+  double stage_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   // constant device tables
   double *d_f = nullptr, *d_f0 = nullptr;
   float2 *d_wrot = nullptr, *d_tw_s = nullptr, *d_tw_m = nullptr;
@@ -224,6 +224,10 @@ struct frbx_handle {
   float2 *d_tree_tw = nullptr;  // [16 s16][Lm/32][2] MBD twiddles of the window-tree fit
   int *d_tree_slot = nullptr;   // [N] channel slot of the window-tree fit
   int tree_s16 = 0;             // slots per residue class mod 16 (0: no window-tree fit)
+  cudaStream_t tree_st[2] = {nullptr, nullptr};             // window-tree chunks alternate
+  cudaEvent_t tree_ev[3] = {nullptr, nullptr, nullptr};
+  std::vector<cudaEvent_t> tree_kev;  // per window-tree chunk: SBD start, SBD end / MBD start, MBD end
+  int tree_chunks = 0;               // chunks of the last window-tree fit (0: another kernel ran)
   void *d_bimg = nullptr;  // BF16 DFT matrix image for the tensor-core fit (if supported)
   int b_bytes = 0, b_atom_bytes = 0, KA = 0, NC = 0;
   int *d_g = nullptr, *d_slot = nullptr;

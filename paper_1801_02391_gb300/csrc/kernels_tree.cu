@@ -14,11 +14,12 @@
 //
 //  k_tree_sbd  gathers the dedispersed one-AP spectrum X(n, j) = w c S(n, j, k + dk(n, j)) and
 //              applies the SBD transform per channel (32-point register FFTs, as in the
-//              segment fit), writing Y[series][k][m][slot] to device memory, where channel n
-//              sits in slot (g_n mod 16) + 16 o (o its rank in that class, empty slots zero);
+//              segment fit), writing Y[series][k][m][n] to device memory;
 //  k_tree_mbd  owns a block of RB SBD rows m of one series and a time tile.  A thread owns 16
-//              cells of one row: for MBD column class q1 (q = q1 + PM q2) and half h it folds
-//              the channel slots (a static loop) into the 16 inputs of one half of a 32-point
+//              cells of one row: its rows of Y go to shared memory with channel n in slot
+//              (g_n mod 16) + 16 o (o its rank in that class; empty slots zero), and for MBD
+//              column class q1 (q = q1 + PM q2) and half h the thread folds the slots (a static
+//              loop) into the 16 inputs of one half of a 32-point
 //              DIF FFT (even or odd q2), runs a 16-point register FFT and walks the cells
 //              through the window tree: the newest matrix of every level is summed with the
 //              anchor of that level (the previous segment needed as first half), emitted, and
@@ -54,24 +55,24 @@ __host__ __device__ inline size_t tree_smem_bytes(int NS, int PM, int RB, int nl
 __global__ void __launch_bounds__(kTreeThreads, 3)
     k_tree_sbd(const __grid_constant__ FitArgs a, const __grid_constant__ TreeArgs t) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int N = a.N, Ls = a.Ls, PS = Ls >> 5, lps = __ffs(PS) - 1, NS = t.NS;
+  const int N = a.N, Ls = a.Ls, PS = Ls >> 5, lps = __ffs(PS) - 1;
   const int JP = a.J1 * 32, xs = JP + 1;
-  float2 *Ys = reinterpret_cast<float2 *>(smem);  // [Ls][NS], channel slots in MBD fold order
-  float2 *X = Ys + Ls * NS;                       // [N][xs]
+  float2 *Ys = reinterpret_cast<float2 *>(smem);  // [Ls][N]
+  float2 *X = Ys + Ls * N;                        // [N][xs]
   float2 *stw = X + N * xs;                       // [PS][xs]
-  for (int i = threadIdx.x; i < Ls * NS; i += blockDim.x) Ys[i] = make_float2(0.f, 0.f);  // empty slots stay 0
   for (int i = threadIdx.x; i < N * xs; i += blockDim.x) X[i] = make_float2(0.f, 0.f);
   for (int i = threadIdx.x; i < PS * JP; i += blockDim.x) {
     const int r = i / JP, c = i - r * JP;
     stw[r * xs + c] = a.sbd_tw[i];
   }
-  const int tile = blockIdx.x % t.n_ktile, s = blockIdx.x / t.n_ktile;
+  // DM trials vary fastest, so the CTAs resident together read the same stretch of the cube
+  const int s = blockIdx.x % t.n_s, tile = blockIdx.x / t.n_s;
   const int2 sd = t.series[s];
   const int kd = a.T - t.dk_max[sd.y];
   const int k_lo = tile * t.k_per_cta, k_hi = min(kd, k_lo + t.k_per_cta);
   const int *dk = a.dk + (size_t)sd.y * a.C;
   float4 *Yout = reinterpret_cast<float4 *>(t.Y + (size_t)s * t.y_series);
-  const int row4 = Ls * NS / 2;  // float4 per AP
+  const int row4 = Ls * N / 2;  // float4 per AP
   __syncthreads();
   for (int k = k_lo; k < k_hi; ++k) {
     // Eq. 3 with l = 1: the dedispersed spectrum of AP k, weighted and rotated
@@ -95,9 +96,8 @@ __global__ void __launch_bounds__(kTreeThreads, 3)
         for (int j2 = 0; j2 < 32; ++j2) A[j2] = cfma(A[j2], xr[j1 * 32 + j2], wr[j1 * 32 + j2]);
       }
       fft32_dif(A);
-      const int sl = __ldg(t.slot_of + n);
 #pragma unroll
-      for (int i = 0; i < 32; ++i) Ys[(m1 + PS * bitrev5(i)) * NS + sl] = A[i];
+      for (int i = 0; i < 32; ++i) Ys[(m1 + PS * bitrev5(i)) * N + n] = A[i];
     }
     __syncthreads();
     const float4 *src = reinterpret_cast<const float4 *>(Ys);
@@ -108,16 +108,6 @@ __global__ void __launch_bounds__(kTreeThreads, 3)
 }
 
 // ----------------------------------------------------------------------------- MBD + tree
-// 16-byte global -> shared copy that bypasses the registers (completes at cp_async_wait).
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-}
-
 // Packed per-thread key: |G|^2 with its 6 low mantissa bits replaced by 32 - q2 (a 2^-17
 // relative truncation, so equal truncated powers prefer the lower q2, i.e. the lower cell).
 __device__ __forceinline__ unsigned cell_key(float2 v, int q2) {
@@ -173,12 +163,16 @@ __global__ void __launch_bounds__(kTreeThreads, 3) k_tree_mbd(const __grid_const
       }
     }
   }
-  const int rbn = RB * NS, rb4 = rbn / 2;  // the block's rows of one AP, in float2 / float4
-  const float2 *Ysrc = t.Y + (size_t)s * t.y_series + (size_t)mb * rbn;
-  const size_t ystep = (size_t)t.Ls * NS;
-  for (int i = tid; i < rb4; i += kTreeThreads)
-    cp_async16(reinterpret_cast<float4 *>(yb) + i, reinterpret_cast<const float4 *>(Ysrc + (size_t)kb * ystep) + i);
-  cp_async_wait();
+  const int rbn = RB * NS, rbg = RB * t.N;  // the block's rows of one AP: slots / channels
+  const float2 *Ysrc = t.Y + (size_t)s * t.y_series + (size_t)mb * rbg;
+  const size_t ystep = (size_t)t.Ls * t.N;
+  // element i of a row block (row i / N, channel i % N) goes to slot (i / N) NS + slot_of(i % N);
+  // a thread moves elements tid + 128 u, the first one prefetched a step ahead
+  auto slot_at = [&](int i) { return (i / t.N) * NS + __ldg(t.slot_of + i % t.N); };
+  const int dst0 = tid < rbg ? slot_at(tid) : -1;
+  for (int i = tid; i < 2 * rbn; i += kTreeThreads) yb[i] = make_float2(0.f, 0.f);
+  __syncthreads();
+  for (int i = tid; i < rbg; i += kTreeThreads) yb[slot_at(i)] = __ldg(Ysrc + (size_t)kb * ystep + i);
   unsigned long long *keys = t.keys + ((size_t)sd.x * t.n_dm + sd.y) * t.S_tot;
   __syncthreads();
 
@@ -189,12 +183,10 @@ __global__ void __launch_bounds__(kTreeThreads, 3) k_tree_mbd(const __grid_const
   // (the level-1 anchor).  Callers alternate the two arrays, so no anchor copy is needed.
   auto ap = [&](const int k, const float2(&prev)[16], float2(&cur)[16]) {
     const int buf = (k - kb) & 1;
-    // next AP's rows into the other buffer while this one is transformed
-    if (k + 1 < ke) {
-      float4 *dst = reinterpret_cast<float4 *>(yb + (buf ^ 1) * rbn);
-      const float4 *src = reinterpret_cast<const float4 *>(Ysrc + (size_t)(k + 1) * ystep);
-      for (int i = tid; i < rb4; i += kTreeThreads) cp_async16(dst + i, src + i);
-    }
+    // next AP's rows: the first element per thread into a register while this one is transformed
+    const bool more = k + 1 < ke;
+    float2 nxt = make_float2(0.f, 0.f);
+    if (more && dst0 >= 0) nxt = __ldg(Ysrc + (size_t)(k + 1) * ystep + tid);
     // MBD: the channels of slot (r, o) = r + 16 o fold into input r of half h of the 32-point
     // DIF FFT (empty slots hold zeros), then a 16-point FFT
     const float2 *yr = yb + buf * rbn + rr * NS;
@@ -253,7 +245,11 @@ __global__ void __launch_bounds__(kTreeThreads, 3) k_tree_mbd(const __grid_const
         }
       }
     }
-    cp_async_wait();
+    if (more) {
+      float2 *yn = yb + (buf ^ 1) * rbn;
+      if (dst0 >= 0) yn[dst0] = nxt;
+      for (int i = tid + kTreeThreads; i < rbg; i += kTreeThreads) yn[slot_at(i)] = __ldg(Ysrc + (size_t)(k + 1) * ystep + i);
+    }
     __syncthreads();
     // merge the block's maxima of the segments emitted at AP k into the series
     if (tid <= E) {
@@ -332,13 +328,13 @@ bool tree_supported(int Ls, int Lm, int N, int J, int s16, const int *windows, i
 
 size_t tree_anchor_floats(int nlev) { return (size_t)tree_global_anchors(nlev) * 16 * kTreeThreads; }
 
-size_t tree_sbd_smem(const FitArgs &a, int NS) {
+size_t tree_sbd_smem(const FitArgs &a) {
   const int JP = a.J1 * 32;
-  return sizeof(float2) * ((size_t)a.Ls * NS + (size_t)a.N * (JP + 1) + (size_t)(a.Ls / 32) * (JP + 1));
+  return sizeof(float2) * ((size_t)a.Ls * a.N + (size_t)a.N * (JP + 1) + (size_t)(a.Ls / 32) * (JP + 1));
 }
 
 cudaError_t launch_tree_sbd(const FitArgs &a, const TreeArgs &t, cudaStream_t st, int64_t *launches) {
-  const size_t smem = tree_sbd_smem(a, t.NS);
+  const size_t smem = tree_sbd_smem(a);
   if (smem > max_smem_optin()) return cudaErrorInvalidConfiguration;
   const long long nb = (long long)t.n_s * t.n_ktile;
   if (nb <= 0) return cudaSuccess;
