@@ -257,7 +257,8 @@ int frbx_create(const frbx_setup *s, frbx_handle **out) {
     // window-tree fit: channel n sits in slot (g_n mod 16) + 16 o of a Y row (o its rank in
     // the class); half h of the 32-point DIF over residues g2 = g_n mod 32 takes it with
     // exp(-2 pi i [(g_n q1 mod Lm) / Lm + h (g_n mod 32) / 32]) -- the MBD twiddle times the
-    // first-stage factor (+1, or -w32^(g mod 16) for the odd half), from the exact index
+    // first-stage factor (+1, or -w32^(g mod 16) for the odd half), from the exact index;
+    // stored as [slot / 2][q1][h][slot mod 2] so a thread reads two slots' twiddles at once
     std::vector<int> cnt16(16, 0);
     tree_slot.resize((size_t)N);
     for (int n = 0; n < N; ++n) {
@@ -273,8 +274,8 @@ int frbx_create(const frbx_setup *s, frbx_handle **out) {
           const long long g = h->g[(size_t)n];
           const long long ex = ((g * q1) % h->Lm) * 32 + hh * (g % 32) * h->Lm;
           const double th = two_pi * (double)(ex % (32LL * h->Lm)) / (32.0 * h->Lm);
-          tree_tw[((size_t)tree_slot[(size_t)n] * PM + q1) * 2 + hh] =
-              make_float2((float)std::cos(th), (float)-std::sin(th));
+          const size_t sl = (size_t)tree_slot[(size_t)n];
+          tree_tw[(((sl >> 1) * PM + q1) * 2 + hh) * 2 + (sl & 1)] = make_float2((float)std::cos(th), (float)-std::sin(th));
         }
   }
   // BF16 DFT matrix of the MBD transform for the tensor-core fit, in its shared-memory image

@@ -147,7 +147,7 @@ struct TreeArgs {
   int emit_w[8];           // window index of level e (window 2^e), -1 = not searched
   int m_lo, m_len, q_lo, q_len;
   const int *slot_of;      // [N] slot of channel n in a Y row: (g_n mod 16) + 16 rank
-  const float2 *tw;        // [NS][PM][2] MBD twiddles folded with the first DIF stage (0: empty)
+  const float2 *tw;        // [NS/2][PM][2][2] MBD twiddles folded with the first DIF stage (0: empty)
   float2 *anc_g;           // deep window-tree anchors, one slice per MBD CTA
 };
 bool tree_supported(int Ls, int Lm, int N, int J, int s16, const int *windows, int n_win, int *nlev);

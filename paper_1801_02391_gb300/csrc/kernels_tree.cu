@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(kTreeThreads, 3) k_tree_mbd(const __grid_const
   const int PM = t.PM, RB = t.RB, Lm = t.Lm;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n_sm = tree_smem_anchors(t.nlev);
-  float2 *tw = reinterpret_cast<float2 *>(smem);  // [NS][PM][2]
+  float2 *tw = reinterpret_cast<float2 *>(smem);  // [NS/2][PM][2][2]
   float2 *yb = tw + NS * PM * 2;                   // [2][RB][NS]
   float2 *anc = yb + 2 * RB * NS;                  // [n_sm][16][128]
   uint2 *red = reinterpret_cast<uint2 *>(anc + n_sm * 16 * kTreeThreads);  // [2][7][4]
@@ -176,7 +176,8 @@ __global__ void __launch_bounds__(kTreeThreads, 3) k_tree_mbd(const __grid_const
   unsigned long long *keys = t.keys + ((size_t)sd.x * t.n_dm + sd.y) * t.S_tot;
   __syncthreads();
 
-  const float2 *twp = tw + q1 * 2 + h;
+  // twiddles of slot pairs: float4 (slot 2p, slot 2p + 1) at [p][q1][h]
+  const float4 *tw4 = reinterpret_cast<const float4 *>(tw) + q1 * 2 + h;
   const int twn = PM * 2;
 
   // One AP: cur receives the one-AP matrix G_1(k) of the thread's cells; prev holds G_1(k - 1)
@@ -189,13 +190,17 @@ __global__ void __launch_bounds__(kTreeThreads, 3) k_tree_mbd(const __grid_const
     if (more && dst0 >= 0) nxt = __ldg(Ysrc + (size_t)(k + 1) * ystep + tid);
     // MBD: the channels of slot (r, o) = r + 16 o fold into input r of half h of the 32-point
     // DIF FFT (empty slots hold zeros), then a 16-point FFT
-    const float2 *yr = yb + buf * rbn + rr * NS;
+    const float4 *yr4 = reinterpret_cast<const float4 *>(yb + buf * rbn + rr * NS);
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
-      float2 z = make_float2(0.f, 0.f);
+    for (int r = 0; r < 16; ++r) cur[r] = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int o = 0; o < S16; ++o) z = cfma(z, yr[r + 16 * o], twp[(r + 16 * o) * twn]);
-      cur[r] = z;
+    for (int o = 0; o < S16; ++o) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {  // slots 16 o + 2 j and 16 o + 2 j + 1, with their twiddles
+        const float4 y = yr4[8 * o + j], w = tw4[(8 * o + j) * twn];
+        cur[2 * j] = cfma(cur[2 * j], make_float2(y.x, y.y), make_float2(w.x, w.y));
+        cur[2 * j + 1] = cfma(cur[2 * j + 1], make_float2(y.z, y.w), make_float2(w.z, w.w));
+      }
     }
     fft16_dif(cur);
     // window tree: level e holds the segment of 2^e APs ending at AP k
@@ -225,12 +230,18 @@ __global__ void __launch_bounds__(kTreeThreads, 3) k_tree_mbd(const __grid_const
       const int w = t.emit_w[e];
       const int k0 = k - (1 << e) + 1;
       if (w >= 0 && k0 >= kb && k0 < kb + t.TT) {  // uniform across the CTA
-        unsigned key = 0u;
+        unsigned kk[16];
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
           const unsigned kc = cell_key(acc[c], 2 * (bitrev5(c) >> 1) + h);
-          key = max(key, (cmask >> c) & 1u ? kc : 0u);
+          kk[c] = (cmask >> c) & 1u ? kc : 0u;
         }
+#pragma unroll
+        for (int wdt = 8; wdt >= 1; wdt >>= 1) {  // pairwise, so the maximum is 4 deep, not 16
+#pragma unroll
+          for (int c = 0; c < wdt; ++c) kk[c] = max(kk[c], kk[c + wdt]);
+        }
+        const unsigned key = kk[0];
         const unsigned wmax = __reduce_max_sync(0xffffffffu, key);
         const unsigned win = __ballot_sync(0xffffffffu, key == wmax);
         if (lane == 0) {
