@@ -298,8 +298,9 @@ int frbx_extract_events(const frbx_event *events, int64_t n_events, int32_t n_se
  *  [6] window-tree fit: device time of its MBD-pass kernels (k_tree_mbd), summed
  *  [7] window-tree fit: number of chunks (= launches of each of the two kernels)
  *  ms_out  [n] out, milliseconds (stages that did not run report 0).
- * Stages [5] and [6] are bracketed by events on the library's own chunk streams; chunks on
- * the two streams overlap, so [5] + [6] can exceed [1].
+ * Stages [5] and [6] are bracketed by events on the library's own streams (SBD passes on
+ * one, MBD passes on the other); the SBD pass of a chunk overlaps the MBD pass of the
+ * previous one, so [5] + [6] can exceed [1].
  * Returns the number of values written (min(n, 8)) or FRBX_EINVAL.
  */
 int frbx_last_stage_times(const frbx_handle *h, double *ms_out, int32_t n);

@@ -57,6 +57,24 @@ cudaError_t upload(T **dst, const std::vector<T> &src) {
 
 bool is_pow2(long long v) { return v > 0 && (v & (v - 1)) == 0; }
 
+// Nearest E4M3 value (1 sign, 4 exponent bits with bias 7, 3 mantissa bits, no infinities,
+// largest finite 448), ties to even, saturating; built from the format's definition.
+uint8_t to_e4m3(double v) {
+  const uint8_t sgn = v < 0 ? 0x80 : 0x00;
+  const double a = std::fabs(v);
+  if (!(a < 448.0)) return sgn | 0x7E;  // 448 = 2^8 x 1.75
+  int e = a > 0 ? (int)std::floor(std::log2(a)) : -6;
+  if (e < -6) e = -6;                    // subnormals share the smallest exponent
+  double r = std::nearbyint(std::ldexp(a, 3 - e));  // mantissa in units of 2^(e-3), ties to even
+  if (r >= 16.0) {
+    r = 8.0;
+    ++e;
+  }
+  if (e > 8 || (e == 8 && r > 14.0)) return sgn | 0x7E;
+  if (r < 8.0) return sgn | (uint8_t)r;  // subnormal (e = -6)
+  return sgn | (uint8_t)(((e + 7) << 3) | ((int)r - 8));
+}
+
 int next_pow2(int v) {
   int p = 1;
   while (p < v) p *= 2;
@@ -282,6 +300,7 @@ int frbx_create(const frbx_setup *s, frbx_handle **out) {
   // (rows: chunks of NC output columns, first half Re G, second half Im G; K-major, 64-wide
   // K atoms, 128-byte swizzle); phases from the exact index g_n q mod Lm, cos/sin in FP64
   std::vector<uint16_t> bimg;
+  std::vector<uint8_t> bimg8;
   if (frbx::mma_supported(h->Ls, h->Lm, N, J)) {
     const int KA = (2 * N + 63) / 64, rows = 2 * h->Lm, NC = std::min(256, rows), half = NC / 2;
     bimg.assign((size_t)KA * rows * 64, 0);
@@ -311,6 +330,25 @@ int frbx_create(const frbx_setup *s, frbx_handle **out) {
     h->NC = NC;
     h->b_atom_bytes = rows * 128;
     h->b_bytes = KA * rows * 128;
+    // E4M3 image: the same rows and swizzle, 128 values per 128-byte row of an atom
+    const int KA8 = (2 * N + 127) / 128;
+    bimg8.assign((size_t)KA8 * rows * 128, 0);
+    auto put8 = [&](int R, int k, double v) {
+      const size_t off = (size_t)(k / 128) * rows * 128 + (size_t)(R / 8) * 1024 + (size_t)(R % 8) * 128 +
+                         (size_t)((((k % 128) / 16) ^ (R % 8)) * 16) + (size_t)(k % 16);
+      bimg8[off] = to_e4m3(v);
+    };
+    for (int R = 0; R < rows; ++R) {
+      const int c = R / NC, r = R % NC, q = c * half + (r % half);
+      const bool im = r >= half;
+      for (int n = 0; n < N; ++n) {
+        const long long ex = ((long long)h->g[(size_t)n] * q) % h->Lm;
+        const double th = two_pi * (double)ex / (double)h->Lm;
+        put8(R, n, im ? -std::sin(th) : std::cos(th));
+        put8(R, N + n, im ? std::cos(th) : std::sin(th));
+      }
+    }
+    h->b_bytes8 = KA8 * rows * 128;
   }
   cudaError_t e = cudaGetDevice(&h->device);
   if (e == cudaSuccess) e = upload(&h->d_f, h->f);
@@ -325,6 +363,7 @@ int frbx_create(const frbx_setup *s, frbx_handle **out) {
   if (e == cudaSuccess) e = upload(&h->d_tree_tw, tree_tw);
   if (e == cudaSuccess) e = upload(&h->d_tree_slot, tree_slot);
   if (e == cudaSuccess && !bimg.empty()) e = upload((uint16_t **)&h->d_bimg, bimg);
+  if (e == cudaSuccess && !bimg8.empty()) e = upload((uint8_t **)&h->d_bimg8, bimg8);
   if (e == cudaSuccess) {
     std::call_once(g_const_once, frbx::set_fft_constants);
     e = cudaGetLastError();
@@ -342,7 +381,7 @@ int frbx_create(const frbx_setup *s, frbx_handle **out) {
 void frbx_destroy(frbx_handle *h) {
   if (!h) return;
   void *ptrs[] = {h->d_f,      h->d_f0,     h->d_wrot, h->d_tw_s, h->d_tw_m,     h->d_g,
-                  h->d_sbd_tw, h->d_mbd_tw, h->d_slot, h->d_bimg, h->d_tree_tw, h->d_tree_slot};
+                  h->d_sbd_tw, h->d_mbd_tw, h->d_slot, h->d_bimg, h->d_tree_tw, h->d_tree_slot, h->d_bimg8};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : h->ev)
@@ -425,8 +464,8 @@ int check_params(frbx_handle *h, const frbx_params *p, int n_bl, FitArgs *a) {
   if (!axis_window(Lm, p->mbd_win_ns, [&](int s) { return ((double)s * 1000.0) / ((double)Lm * dfg); },
                    &a->q_lo, &a->q_len))
     return fail(h, FRBX_EINVAL, "MBD window holds no grid cell");
-  if (p->kernel < 0 || p->kernel > 4) return fail(h, FRBX_EINVAL, "kernel must be 0, 1, 2, 3 or 4");
-  if (p->kernel == 3) {
+  if (p->kernel < 0 || p->kernel > 5) return fail(h, FRBX_EINVAL, "kernel must be 0 to 5");
+  if (p->kernel == 3 || p->kernel == 5) {
     if (!h->d_bimg) return fail(h, FRBX_EUNSUPPORTED, "tensor-core fit needs Ls of 64 or 128, 2 Lm >= 32, N <= 64");
     if (a->m_len != Ls || a->q_len != Lm)
       return fail(h, FRBX_EUNSUPPORTED, "tensor-core fit searches the whole grid (no delay windows)");
@@ -499,15 +538,17 @@ void to_cand(const frbx_handle *h, const frbx::Pulse &p, const double *dm, const
 }
 
 // Tensor-core fit of n_valid segments (implicit layout of the search, or the list in a).
-int run_fit_mma(frbx_handle *h, const FitArgs &a, int n_bl, bool list_mode, long long n_valid, cudaStream_t st) {
+int run_fit_mma(frbx_handle *h, const FitArgs &a, int n_bl, bool list_mode, long long n_valid, bool fp8,
+                cudaStream_t st) {
   frbx::MmaArgs mm{};
-  mm.bimg = h->d_bimg;
-  mm.b_bytes = h->b_bytes;
+  mm.fp8 = fp8 ? 1 : 0;
+  mm.bimg = fp8 ? h->d_bimg8 : h->d_bimg;
+  mm.b_bytes = fp8 ? h->b_bytes8 : h->b_bytes;
   mm.b_atom_bytes = h->b_atom_bytes;
   mm.KA = h->KA;
   mm.NC = h->NC;
   mm.n_chunk = 2 * h->Lm / h->NC;
-  mm.kk_steps = (2 * h->N + 15) / 16;
+  mm.kk_steps = fp8 ? (2 * h->N + 31) / 32 : (2 * h->N + 15) / 16;  // K per MMA: 32 (E4M3), 16 (BF16)
   int cols = 32;
   while (cols < 2 * h->NC) cols *= 2;
   mm.tmem_cols = cols;
@@ -602,12 +643,11 @@ int run_fit_tree(frbx_handle *h, const FitArgs &a, const frbx_params &p, int nle
   if (!ser.empty()) {
     size_t free_b = 0, total_b = 0;
     FRBX_CK(h, cudaMemGetInfo(&free_b, &total_b));
-    // per series: its transformed spectra and the deep anchors of its MBD CTAs.  Chunks
-    // alternate between two streams, each with its own spectra and anchor buffers, so the SBD
-    // pass of one chunk and the tail of the other chunk's MBD pass overlap.
+    // per series: its transformed spectra and the deep anchors of its MBD CTAs, two sets so
+    // consecutive chunks use different buffers.
     const size_t anc_per = sizeof(float2) * frbx::tree_anchor_floats(nlev) * t.n_mb * t.n_tt;
     const size_t per = sizeof(float2) * t.y_series + anc_per;
-    const size_t budget = std::max(per, std::min<size_t>((size_t)8 << 30, (free_b + h->ytree.bytes) / 4));
+    const size_t budget = std::max(per, std::min<size_t>((size_t)16 << 30, (free_b + h->ytree.bytes) / 4));
     const size_t chunk = std::max<size_t>(1, std::min(ser.size(), budget / per));
     const size_t ser_bytes = (sizeof(int2) * ser.size() + 255) & ~(size_t)255;
     const size_t y_bytes = (sizeof(float2) * t.y_series * chunk + 255) & ~(size_t)255;
@@ -615,41 +655,52 @@ int run_fit_tree(frbx_handle *h, const FitArgs &a, const frbx_params &p, int nle
     FRBX_CK(h, ensure(h->ytree, ser_bytes + 2 * (y_bytes + a_bytes)));
     int2 *d_ser = (int2 *)h->ytree.p;
     FRBX_CK(h, cudaMemcpyAsync(d_ser, ser.data(), sizeof(int2) * ser.size(), cudaMemcpyHostToDevice, st));
-    for (int i = 0; i < 2; ++i) {
+    // the SBD passes run on one library stream and the MBD passes on the other, so the SBD
+    // pass of chunk i + 1 overlaps the MBD pass of chunk i; chunk parity picks the buffers
+    for (int i = 0; i < 2; ++i)
       if (!h->tree_st[i]) FRBX_CK(h, cudaStreamCreateWithFlags(&h->tree_st[i], cudaStreamNonBlocking));
-      if (!h->tree_ev[i]) FRBX_CK(h, cudaEventCreateWithFlags(&h->tree_ev[i], cudaEventDisableTiming));
-    }
-    if (!h->tree_ev[2]) FRBX_CK(h, cudaEventCreateWithFlags(&h->tree_ev[2], cudaEventDisableTiming));
-    FRBX_CK(h, cudaEventRecord(h->tree_ev[2], st));
-    for (int i = 0; i < 2; ++i) FRBX_CK(h, cudaStreamWaitEvent(h->tree_st[i], h->tree_ev[2], 0));
+    for (cudaEvent_t &ev : h->tree_ev)
+      if (!ev) FRBX_CK(h, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    cudaStream_t sA = h->tree_st[0], sB = h->tree_st[1];
+    cudaEvent_t ev_start = h->tree_ev[0], *evA = h->tree_ev + 1, *evB = h->tree_ev + 3;
+    FRBX_CK(h, cudaEventRecord(ev_start, st));
+    FRBX_CK(h, cudaStreamWaitEvent(sA, ev_start, 0));
+    FRBX_CK(h, cudaStreamWaitEvent(sB, ev_start, 0));
     const int n_chunks = (int)((ser.size() + chunk - 1) / chunk);
-    while ((int)h->tree_kev.size() < 3 * n_chunks) {
+    while ((int)h->tree_kev.size() < 4 * n_chunks) {
       cudaEvent_t ev = nullptr;
       FRBX_CK(h, cudaEventCreate(&ev));
       h->tree_kev.push_back(ev);
     }
     h->tree_chunks = n_chunks;
-    int par = 0, ci = 0;
-    for (size_t c0 = 0; c0 < ser.size(); c0 += chunk, par ^= 1, ++ci) {
+    int ci = 0;
+    for (size_t c0 = 0; c0 < ser.size(); c0 += chunk, ++ci) {
+      const int par = ci & 1;
       frbx::TreeArgs tc = t;
       char *base = (char *)h->ytree.p + ser_bytes + (size_t)par * (y_bytes + a_bytes);
       tc.Y = (float2 *)base;
       tc.anc_g = (float2 *)(base + y_bytes);
       tc.series = d_ser + c0;
       tc.n_s = (int)std::min(chunk, ser.size() - c0);
-      cudaEvent_t *kev = h->tree_kev.data() + 3 * ci;
-      cudaError_t e = cudaEventRecord(kev[0], h->tree_st[par]);
-      if (e == cudaSuccess) e = frbx::launch_tree_sbd(a, tc, h->tree_st[par], &h->launches);
-      if (e == cudaSuccess) e = cudaEventRecord(kev[1], h->tree_st[par]);
-      if (e == cudaSuccess) e = frbx::launch_tree_mbd(tc, full, h->tree_st[par], &h->launches);
-      if (e == cudaSuccess) e = cudaEventRecord(kev[2], h->tree_st[par]);
+      cudaEvent_t *kev = h->tree_kev.data() + 4 * ci;
+      cudaError_t e = cudaSuccess;
+      if (ci >= 2) e = cudaStreamWaitEvent(sA, evB[par], 0);  // the MBD pass two chunks back is done with Y[par]
+      if (e == cudaSuccess) e = cudaEventRecord(kev[0], sA);
+      if (e == cudaSuccess) e = frbx::launch_tree_sbd(a, tc, sA, &h->launches);
+      if (e == cudaSuccess) e = cudaEventRecord(kev[1], sA);
+      if (e == cudaSuccess) e = cudaEventRecord(evA[par], sA);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(sB, evA[par], 0);
+      if (e == cudaSuccess) e = cudaEventRecord(kev[2], sB);
+      if (e == cudaSuccess) e = frbx::launch_tree_mbd(tc, full, sB, &h->launches);
+      if (e == cudaSuccess) e = cudaEventRecord(kev[3], sB);
+      if (e == cudaSuccess) e = cudaEventRecord(evB[par], sB);
       if (e == cudaErrorInvalidConfiguration) return fail(h, FRBX_EUNSUPPORTED, "window-tree fit does not fit this shape");
       FRBX_CK(h, e);
     }
-    for (int i = 0; i < 2; ++i) {
-      FRBX_CK(h, cudaEventRecord(h->tree_ev[i], h->tree_st[i]));
-      FRBX_CK(h, cudaStreamWaitEvent(st, h->tree_ev[i], 0));
-    }
+    FRBX_CK(h, cudaEventRecord(evA[0], sA));
+    FRBX_CK(h, cudaStreamWaitEvent(st, evA[0], 0));
+    FRBX_CK(h, cudaEventRecord(evB[0], sB));
+    FRBX_CK(h, cudaStreamWaitEvent(st, evB[0], 0));
   }
   FRBX_CK(h, frbx::launch_tree_finalize(a.out, (long long)n_el, S_tot, n_dm, n_win, d_tab, d_tab + frbx::kMaxWin,
                                          d_tab + 3 * frbx::kMaxWin, a.log2Lm, h->Lm, st, &h->launches));
@@ -716,10 +767,10 @@ int finish_search(frbx_handle *h, const frbx_seg *series, int n_bl, int T, const
     // window-tree fit: device time of its SBD and MBD kernels, summed over the chunks
     h->stage_ms[5] = h->stage_ms[6] = h->stage_ms[7] = 0.0;
     for (int c = 0; c < h->tree_chunks; ++c) {
-      const cudaEvent_t *kev = h->tree_kev.data() + 3 * c;
+      const cudaEvent_t *kev = h->tree_kev.data() + 4 * c;
       FRBX_CK(h, cudaEventElapsedTime(&ms, kev[0], kev[1]));
       h->stage_ms[5] += ms;
-      FRBX_CK(h, cudaEventElapsedTime(&ms, kev[1], kev[2]));
+      FRBX_CK(h, cudaEventElapsedTime(&ms, kev[2], kev[3]));
       h->stage_ms[6] += ms;
     }
     h->stage_ms[7] = h->tree_chunks;
@@ -832,8 +883,8 @@ extern "C" int frbx_fit_segments(frbx_handle *h, const void *vis, int32_t vis_on
   a.n_seg = n_seg;
   a.tile = 16;
   a.out = (frbx_seg *)h->series.p;
-  if (p.kernel == 3) {
-    rc = run_fit_mma(h, a, n_bl, true, n_seg, st);
+  if (p.kernel == 3 || p.kernel == 5) {
+    rc = run_fit_mma(h, a, n_bl, true, n_seg, p.kernel == 5, st);
     if (rc) return rc;
   } else {
     cudaError_t e = frbx::launch_fit(a, n_bl, true, p.kernel, st, &h->launches);
@@ -926,10 +977,10 @@ extern "C" int frbx_search(frbx_handle *h, const void *vis, int32_t vis_on_devic
   if (p.kernel == 4 || (p.kernel == 0 && tree_ok)) {
     rc = run_fit_tree(h, a, p, nlev, windows, n_win, dkm, n_bl, T, n_dm, d_tab, L.S_tot, st);
     if (rc) return rc;
-  } else if (p.kernel == 3) {
+  } else if (p.kernel == 3 || p.kernel == 5) {
     long long nv = 0;
     for (int v : L.n_valid) nv += v;
-    rc = run_fit_mma(h, a, n_bl, false, nv * n_bl, st);
+    rc = run_fit_mma(h, a, n_bl, false, nv * n_bl, p.kernel == 5, st);
     if (rc) return rc;
   } else {
     cudaError_t e = frbx::launch_fit(a, n_bl, false, p.kernel, st, &h->launches);

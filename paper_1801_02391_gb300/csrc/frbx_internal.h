@@ -89,6 +89,7 @@ struct MmaArgs {
   long long n_items;       // implicit layout: n_bl * ceil(T / TT) * n_dm work items
   int *err;                // device flag, set to FRBX_ETIMEOUT when a bounded wait gives up
   long long timeout;       // clock cycles per wait
+  int fp8;                 // 1: A and B in E4M3 (kind::f8f6f4), A scaled per segment
 };
 bool mma_supported(int Ls, int Lm, int N, int J);
 void set_mma_constants();
@@ -224,12 +225,13 @@ struct frbx_handle {
   float2 *d_tree_tw = nullptr;  // [16 s16][Lm/32][2] MBD twiddles of the window-tree fit
   int *d_tree_slot = nullptr;   // [N] channel slot of the window-tree fit
   int tree_s16 = 0;             // slots per residue class mod 16 (0: no window-tree fit)
-  cudaStream_t tree_st[2] = {nullptr, nullptr};             // window-tree chunks alternate
-  cudaEvent_t tree_ev[3] = {nullptr, nullptr, nullptr};
-  std::vector<cudaEvent_t> tree_kev;  // per window-tree chunk: SBD start, SBD end / MBD start, MBD end
+  cudaStream_t tree_st[2] = {nullptr, nullptr};  // window-tree fit: SBD passes, MBD passes
+  cudaEvent_t tree_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // start, SBD done x2, MBD done x2
+  std::vector<cudaEvent_t> tree_kev;  // per window-tree chunk: SBD start / end, MBD start / end
   int tree_chunks = 0;               // chunks of the last window-tree fit (0: another kernel ran)
   void *d_bimg = nullptr;  // BF16 DFT matrix image for the tensor-core fit (if supported)
-  int b_bytes = 0, b_atom_bytes = 0, KA = 0, NC = 0;
+  void *d_bimg8 = nullptr;  // the same matrix in E4M3
+  int b_bytes = 0, b_bytes8 = 0, b_atom_bytes = 0, KA = 0, NC = 0;
   int *d_g = nullptr, *d_slot = nullptr;
   // scratch, grown on demand
   struct Buf {

@@ -1,4 +1,4 @@
-// Segment fit with the MBD transform as a BF16 DFT-GEMM on the tcgen05 tensor cores
+// Segment fit with the MBD transform as a BF16 or FP8 (E4M3) DFT-GEMM on the tcgen05 tensor cores
 // (Eq. 3 gather and the SBD transform in FP32 on the CUDA cores, Eq. 5's sum over channels
 // as a dense GEMM with FP32 accumulation in tensor memory, grid maximum on the CUDA cores).
 //
@@ -8,14 +8,20 @@
 //     B rows of a chunk: first NC/2 give Re G(m, q), the next NC/2 give Im G(m, q) with
 //     Re G = sum_n Re Y cos th + Im Y sin th,  Im G = sum_n Im Y cos th - Re Y sin th,
 //     th = 2 pi (g_n q mod Lm) / Lm  (the phase index is exact; only cos/sin are rounded).
+// FP8 form: A holds s Y in E4M3 with s the power of two for which s times the L1 norm of the
+// segment's spectrum is at most 448 (so no element can leave E4M3's finite range), B holds
+// cos / sin in E4M3, the MMA is kind::f8f6f4 with K = 32 per instruction, and the epilogue
+// divides the segment's maximum |G|^2 by s^2.
 //
-// Roles (288 threads):  warps 0-3 gather + SBD FFT -> A tile (BF16, 128B-swizzled, K-major);
-// warp 8 allocates tensor memory and one lane issues tcgen05.mma per chunk into one of two
-// accumulator slots; warps 4-7 read the slot back with tcgen05.ld (warp w reads lanes
+// Roles (416 threads): two producer groups (warps 0-3 and 4-7) each gather a segment and run
+// its SBD FFT into an A tile (BF16, 128B-swizzled, K-major) of a three-tile ring; warp 12
+// allocates tensor memory and one lane issues tcgen05.mma per chunk into one of two
+// accumulator slots; warps 8-11 read the slot back with tcgen05.ld (warp w reads lanes
 // 32 (w % 4) ..), form |G|^2 and keep the maximum.  Hand-offs use mbarriers; every wait is
 // bounded by a clock limit after which the kernel records FRBX_ETIMEOUT, drains, frees its
 // tensor memory and returns.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include "fft32.cuh"
 #include "fit_common.cuh"
@@ -37,6 +43,7 @@ constexpr int kAtomBytes = kRows * 128;            // one 64-wide K atom of an A
 constexpr int kGatherBatch = 16;                   // independent loads in flight per thread
 constexpr int kBarGroup0 = 1, kBarEpi = 3;         // named barrier ids (group g uses 1 + g)
 constexpr int kListItem = 64;                      // list mode: rows per work item
+constexpr int kScaleRing = 16;                     // FP8: per-tile segment scales in flight
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -71,6 +78,12 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t addr) {
 __device__ __forceinline__ uint32_t a_offset(int row, int k) {
   return (uint32_t)((k >> 6) * kAtomBytes + (row >> 3) * 1024 + (row & 7) * 128 +
                     ((((k & 63) >> 3) ^ (row & 7)) << 4) + (k & 7) * 2);
+}
+
+// byte offset of FP8 element (row, k): the same 128-byte rows and swizzle, 128 values per row
+__device__ __forceinline__ uint32_t a_offset8(int row, int k) {
+  return (uint32_t)((k >> 7) * kAtomBytes + (row >> 3) * 1024 + (row & 7) * 128 +
+                    ((((k & 127) >> 4) ^ (row & 7)) << 4) + (k & 15));
 }
 
 __device__ __forceinline__ void named_sync(int id, int n) {
@@ -174,6 +187,7 @@ struct Cursor {
 
 }  // namespace
 
+template <bool kFp8>
 __global__ void __launch_bounds__(kMmaThreads, 1)
     k_fit_mma(const __grid_constant__ FitArgs a, const __grid_constant__ MmaArgs mm, int list) {
   extern __shared__ unsigned char smem_raw[];
@@ -184,6 +198,10 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
   __shared__ float red_p[kEpiWarps];
   __shared__ int red_i[kEpiWarps];
   __shared__ ItemTab tabs[kGroups + 1];  // producer groups, epilogue
+  // FP8: 1/s^2 of each segment of a tile (A holds s Y, s a power of two), tagged by tile number
+  __shared__ float sc_inv2[kScaleRing][2];
+  __shared__ long long sc_tag[kScaleRing];
+  __shared__ float l1_part[kGroups][kGroupWarps];
 
   const int N = a.N, Ls = a.Ls, Lm = a.Lm, C = a.C;
   const int PS = Ls >> 5, lps = __ffs(PS) - 1;
@@ -220,6 +238,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
     }
     mbar_init(&bar_drain, 1);
     abort_flag = 0;
+    for (int i = 0; i < kScaleRing; ++i) sc_tag[i] = -1;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == kMmaWarp) {
@@ -279,6 +298,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
             d = tab.d;
           }
           // gather: kGatherBatch independent point loads in flight per thread
+          float l1 = 0.f;
           const int *dk = a.dk + (size_t)d * C;
           const float2 *vb = a.vis + (size_t)bl * a.T * C;
           for (int p0 = gtid; p0 < C; p0 += kGroupThreads * kGatherBatch) {
@@ -306,11 +326,30 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
               const int c = p0 + q * kGroupThreads;
               if (c < C) {
                 const int n = c / a.J, j = c - n * a.J;
-                X[n * L.xs + j] = cmul(acc[q], __ldg(a.wrot + c));
+                const float2 x = cmul(acc[q], __ldg(a.wrot + c));
+                X[n * L.xs + j] = x;
+                if (kFp8) l1 += fabsf(x.x) + fabsf(x.y);
               }
             }
           }
+          if (kFp8) {
+#pragma unroll
+            for (int off = 16; off; off >>= 1) l1 += __shfl_xor_sync(0xffffffffu, l1, off);
+            if (lane == 0) l1_part[g][gtid >> 5] = l1;
+          }
           named_sync(bar, kGroupThreads);
+          // FP8: every |Re Y|, |Im Y| is at most the L1 norm of the segment's spectrum, so the
+          // power of two s with s L1 <= 448 keeps A within E4M3's finite range
+          float sc = 1.f;
+          if (kFp8) {
+            float tot = 0.f;
+#pragma unroll
+            for (int w = 0; w < kGroupWarps; ++w) tot += l1_part[g][w];
+            int ex = 1;
+            if (tot > 1e-30f) frexpf(448.f / tot, &ex);
+            sc = ldexpf(1.f, max(-100, min(100, ex - 1)));
+            if (gtid == 0) sc_inv2[i % kScaleRing][sl] = 1.f / (sc * sc);
+          }
           // SBD four-step FFT, task (n, m1); rows sl * Ls + m of the A tile
           for (int t = gtid; t < N * PS; t += kGroupThreads) {
             const int n = t >> lps, m1 = t & (PS - 1);
@@ -327,12 +366,18 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
 #pragma unroll
             for (int q = 0; q < 32; ++q) {
               const int row = sl * Ls + m1 + PS * bitrev5(q);
-              *reinterpret_cast<__nv_bfloat16 *>(At + a_offset(row, n)) = __float2bfloat16_rn(A[q].x);
-              *reinterpret_cast<__nv_bfloat16 *>(At + a_offset(row, N + n)) = __float2bfloat16_rn(A[q].y);
+              if (kFp8) {
+                At[a_offset8(row, n)] = (unsigned char)__nv_cvt_float_to_fp8(A[q].x * sc, __NV_SATFINITE, __NV_E4M3);
+                At[a_offset8(row, N + n)] = (unsigned char)__nv_cvt_float_to_fp8(A[q].y * sc, __NV_SATFINITE, __NV_E4M3);
+              } else {
+                *reinterpret_cast<__nv_bfloat16 *>(At + a_offset(row, n)) = __float2bfloat16_rn(A[q].x);
+                *reinterpret_cast<__nv_bfloat16 *>(At + a_offset(row, N + n)) = __float2bfloat16_rn(A[q].y);
+              }
             }
           }
           named_sync(bar, kGroupThreads);  // X is reused by the next segment
         }
+        if (kFp8 && gtid == 0) sc_tag[i % kScaleRing] = i;
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(&bar_afull[b]);
       }
@@ -345,7 +390,9 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
     // ================= MMA issuer =================
     long long i = 0, chunk_ctr = 0;
     bool ok = true;
-    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(mm.NC >> 3) << 17) |
+    // D = F32; A, B = BF16 (kind::f16) or E4M3 (kind::f8f6f4, format code 0); K-major; N, M
+    const uint32_t ab = kFp8 ? 0u : 1u;
+    const uint32_t idesc = (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(mm.NC >> 3) << 17) |
                            ((uint32_t)(kRows >> 4) << 24);
     for (long long item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
       const int tiles = list ? (int)((min((long long)kListItem, mm.n_valid - item * kListItem) + SPT - 1) / SPT)
@@ -375,8 +422,12 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
               const uint64_t bd = desc_sw128(su32(sB) + (uint32_t)((kk >> 2) * mm.b_atom_bytes) +
                                              (uint32_t)(c * mm.NC * 128) + (uint32_t)((kk & 3) * 32));
               const uint32_t accum = kk > 0 ? 1u : 0u;
-              asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
-                           ::"r"(d_tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(accum) : "memory");
+              if (kFp8)
+                asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n"
+                             ::"r"(d_tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(accum) : "memory");
+              else
+                asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                             ::"r"(d_tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(accum) : "memory");
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                          ::"r"(su32(&bar_accfull[s])) : "memory");
@@ -409,7 +460,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
     const int half = mm.NC >> 1;               // q values per chunk
     const int qpart = half;                    // q values this warp reads per chunk (>= 16)
     ItemTab &tab = tabs[kGroups];
-    long long chunk_ctr = 0;
+    long long chunk_ctr = 0, ie = 0;  // ie: CTA-local tile number, as the producers count
     bool ok = true;
     for (long long item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
       if (etid == 0) {
@@ -422,7 +473,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
       }
       named_sync(kBarEpi, kEpiWarps * 32);
       const int tiles = tab.tiles, nseg = tab.nseg;
-      for (int ti = 0; ti < tiles; ++ti) {
+      for (int ti = 0; ti < tiles; ++ti, ++ie) {
         float bp = -1.f;
         int bq = 0;
         for (int c = 0; c < mm.n_chunk; ++c, ++chunk_ctr) {
@@ -494,6 +545,14 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
               int l, k0;
               item_segment(a, tab, k, a.n_win, l, k0, out);
             }
+            if (kFp8) {  // undo the segment's scale (its tag proves the entry is this tile's)
+              const volatile long long *tag = sc_tag + ie % kScaleRing;
+              const long long t0 = clock64();
+              while (*tag != ie && clock64() - t0 < mm.timeout) {
+              }
+              if (*tag != ie) *abortp = 1;
+              fp *= sc_inv2[ie % kScaleRing][sl];
+            }
             frbx_seg r;
             r.amp = sqrtf(fp);
             r.sbd_idx = (uint16_t)(fi >> a.log2Lm);
@@ -554,9 +613,10 @@ cudaError_t launch_fit_mma(const FitArgs &a, const MmaArgs &mm, int n_bl, bool l
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const long long units = list_mode ? (mm.n_valid + kListItem - 1) / kListItem : mm.n_items;
   const unsigned grid = (unsigned)(units < sms ? units : sms);
-  cudaError_t e = cudaFuncSetAttribute(k_fit_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
+  auto kern = mm.fp8 ? k_fit_mma<true> : k_fit_mma<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.bytes);
   if (e != cudaSuccess) return e;
-  k_fit_mma<<<grid, kMmaThreads, L.bytes, st>>>(a, mm, list_mode ? 1 : 0);
+  kern<<<grid, kMmaThreads, L.bytes, st>>>(a, mm, list_mode ? 1 : 0);
   ++*launches;
   return cudaGetLastError();
 }
