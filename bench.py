@@ -405,42 +405,43 @@ def main():
             "gpu_launches": launches, "roofline": roof, "clocks": clocks,
             "stages_ms": stages, "segments_per_step": n_seg,
             "pulses": int(out["counts"]["pulses"]), "groups": int(out["counts"]["groups"])}
-    # the tensor-core form (MBD transform as a BF16 DFT-GEMM on tcgen05), same workload
+    # the tensor-core forms (MBD transform as a BF16 / FP8 DFT-GEMM on tcgen05), same workload
+    line_variants = {}
     if not args.no_variants and args.kernel == 0 and h.Ls in (64, 128):
-        try:
-            for _ in range(1):
-                h.search(vis_dev, wl.dms, wl.windows, combos=combos, kernel=3, stream=stream)
-            barrier()
-            v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            vsteps = max(1, min(2, args.steps))
-            vfit = []
-            v0.record(stream)
-            for _ in range(vsteps):
-                o3 = h.search(vis_dev, wl.dms, wl.windows, combos=combos, kernel=3, stream=stream)
-                vfit.append(h.stage_times()["fit"])
-            v1.record(stream)
-            torch.cuda.synchronize()
-            vms = max_over_ranks(v0.elapsed_time(v1) / vsteps)
-            gflops = n_seg * gemm_flops_per_segment(wl.n_chan, h.Ls, h.Lm)
-            vach = gflops / (statistics.mean(vfit) / 1e3) / 1e12
-            line_variants = {"tensor_bf16": {
-                "value": world * cells / (vms / 1e3), "unit": "cells/s", "ms_per_step": vms, "steps": vsteps,
-                "dtype": "bf16 operands, f32 accumulate (MBD DFT-GEMM); f32 elsewhere",
-                "roofline": {"bound": "tensor", "kernel": "k_fit_mma", "achieved": vach,
-                             "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
-                             "frac": vach / peaks["bf16_tflops_sustained"], "traffic": None,
-                             "peak_kind": peaks_kind + " sustained bf16",
-                             "work": f"{n_seg} segments x {gemm_flops_per_segment(wl.n_chan, h.Ls, h.Lm):.0f} flop "
-                                     "(dense DFT-GEMM of the MBD transform)",
-                             "fit_ms": statistics.mean(vfit)},
-                "pulses": int(o3["counts"]["pulses"]), "groups": int(o3["counts"]["groups"])}}
-        except Exception as exc:  # a variant that cannot run on this setup is reported, not fatal
-            line_variants = {"tensor_bf16": {"unavailable": str(exc)}}
-    else:
-        line_variants = None
+        for vname, vk, vdt in (("tensor_bf16", 3, "bf16 operands, f32 accumulate (MBD DFT-GEMM); f32 elsewhere"),
+                               ("tensor_fp8", 5, "fp8 e4m3 operands (A scaled per segment), f32 accumulate "
+                                                 "(MBD DFT-GEMM); f32 elsewhere")):
+            try:
+                h.search(vis_dev, wl.dms, wl.windows, combos=combos, kernel=vk, stream=stream)
+                barrier()
+                v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                vsteps = 1
+                vfit = []
+                v0.record(stream)
+                for _ in range(vsteps):
+                    o3 = h.search(vis_dev, wl.dms, wl.windows, combos=combos, kernel=vk, stream=stream)
+                    vfit.append(h.stage_times()["fit"])
+                v1.record(stream)
+                torch.cuda.synchronize()
+                vms = max_over_ranks(v0.elapsed_time(v1) / vsteps)
+                gflops = n_seg * gemm_flops_per_segment(wl.n_chan, h.Ls, h.Lm)
+                vach = gflops / (statistics.mean(vfit) / 1e3) / 1e12
+                # the measured BF16 peak; FP8 dense tensor rate is twice BF16's (nominal ratio)
+                vpeak = peaks["bf16_tflops_sustained"] * (2.0 if vk == 5 else 1.0)
+                line_variants[vname] = {
+                    "value": world * cells / (vms / 1e3), "unit": "cells/s", "ms_per_step": vms, "steps": vsteps,
+                    "dtype": vdt,
+                    "roofline": {"bound": "tensor", "kernel": "k_fit_mma", "achieved": vach, "peak": vpeak,
+                                 "unit": "TFLOP/s", "frac": vach / vpeak, "traffic": None,
+                                 "peak_kind": peaks_kind + " sustained bf16" + (" x 2 (fp8 nominal ratio)" if vk == 5 else ""),
+                                 "work": f"{n_seg} segments x {gemm_flops_per_segment(wl.n_chan, h.Ls, h.Lm):.0f} flop "
+                                         "(dense DFT-GEMM of the MBD transform)",
+                                 "fit_ms": statistics.mean(vfit)},
+                    "pulses": int(o3["counts"]["pulses"]), "groups": int(o3["counts"]["groups"])}
+            except Exception as exc:  # a variant that cannot run on this setup is reported, not fatal
+                line_variants[vname] = {"unavailable": str(exc)}
     if not args.no_variants and args.kernel == 0:
         try:
-            line_variants = line_variants or {}
             line_variants["batch"] = run_batch_variant(frbx, torch, stream, args.batch_bl, args.batch_scale,
                                                        max(1, args.batch_steps), barrier)
         except Exception as exc:
