@@ -388,8 +388,9 @@ def main():
                 "hbm_frac_8B_per_cell": hbm_frac, "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_kind": peaks_kind}
     else:
         achieved = flops / (fit_mean / 1e3) / 1e12
-        roof = {"bound": "alu", "kernel": "k_fit_fft" if (h.Ls % 32 == 0 and h.Lm % 32 == 0 and args.kernel != 1)
-                else "k_fit_direct", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+        kname = ("k_fit_mma" if args.kernel in (3, 5) else
+                 "k_fit_fft" if (h.Ls % 32 == 0 and h.Lm % 32 == 0 and args.kernel != 1) else "k_fit_direct")
+        roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP32_PEAK_TFLOPS,
                 "traffic": None if FIT_DRAM_BYTES_PER_SEGMENT is None else FIT_DRAM_BYTES_PER_SEGMENT * n_seg,
                 "peak_note": "FP32 CUDA-core peak 152 SM x 128 lanes x 2 flop x 2070 MHz (derived, not measured)",

@@ -601,18 +601,28 @@ int run_stats(frbx_handle *h, StatsArgs sa, cudaStream_t st, std::vector<frbx_ev
 // builds every window from them and merges the maxima into the series buffer (as 64-bit
 // keys, zeroed first); a last pass turns the keys into frbx_seg records.  d_tab holds the
 // window tables and valid-segment counts in the layout frbx_search uploads.
-int run_fit_tree(frbx_handle *h, const FitArgs &a, const frbx_params &p, int nlev, const int32_t *windows, int n_win,
-                 const std::vector<int> &dkm, int n_bl, int T, int n_dm, const int *d_tab, int S_tot, cudaStream_t st) {
-  const size_t n_el = (size_t)n_bl * n_dm * S_tot;
-  if (n_el == 0) return FRBX_OK;
-  FRBX_CK(h, cudaMemsetAsync(a.out, 0, sizeof(frbx_seg) * n_el, st));
+struct TreeRun {
   frbx::TreeArgs t{};
+  bool full = true;
+  std::vector<int2> ser;  // (bl, d) of the series whose sweep fits the scan, baseline-major
+  size_t chunk = 1, y_bytes = 0, a_bytes = 0;
+  int n_bl = 0;
+  size_t need() const { return 2 * (y_bytes + a_bytes); }  // two buffer sets: chunks alternate
+};
+
+// Host planning: kernel arguments, series list and chunk size for `budget` bytes per set.
+void plan_tree(const frbx_handle *h, const FitArgs &a, int nlev, const int32_t *windows, int n_win,
+               const std::vector<int> &dkm, int n_bl, int T, int n_dm, const int *win_off, int S_tot, size_t budget,
+               TreeRun *r) {
+  frbx::TreeArgs &t = r->t;
+  t = frbx::TreeArgs{};
+  r->n_bl = n_bl;
   t.dk_max = (const int *)h->dk_max.p;
   t.T = T;
   t.keys = reinterpret_cast<unsigned long long *>(a.out);
   t.n_dm = n_dm;
   t.S_tot = S_tot;
-  t.win_off = d_tab + frbx::kMaxWin;
+  t.win_off = win_off;
   t.N = h->N;
   t.NS = 16 * h->tree_s16;
   t.slot_of = h->d_tree_slot;
@@ -634,65 +644,64 @@ int run_fit_tree(frbx_handle *h, const FitArgs &a, const frbx_params &p, int nle
   t.k_per_cta = 16;
   t.n_ktile = (T + t.k_per_cta - 1) / t.k_per_cta;
   t.y_series = (size_t)T * h->Ls * h->N;
-  const bool full = a.m_lo == 0 && a.m_len == h->Ls && a.q_lo == 0 && a.q_len == h->Lm;
-  // series whose dispersion sweep fits the scan, baseline-major
-  std::vector<int2> ser;
+  r->full = a.m_lo == 0 && a.m_len == h->Ls && a.q_lo == 0 && a.q_len == h->Lm;
+  r->ser.clear();
   for (int b = 0; b < n_bl; ++b)
     for (int d = 0; d < n_dm; ++d)
-      if (T - dkm[(size_t)d] >= 1) ser.push_back(make_int2(b, d));
-  if (!ser.empty()) {
-    size_t free_b = 0, total_b = 0;
-    FRBX_CK(h, cudaMemGetInfo(&free_b, &total_b));
-    // per series: its transformed spectra and the deep anchors of its MBD CTAs, two sets so
-    // consecutive chunks use different buffers.
-    const size_t anc_per = sizeof(float2) * frbx::tree_anchor_floats(nlev) * t.n_mb * t.n_tt;
-    const size_t per = sizeof(float2) * t.y_series + anc_per;
-    const size_t budget = std::max(per, std::min<size_t>((size_t)16 << 30, (free_b + h->ytree.bytes) / 4));
-    const size_t chunk = std::max<size_t>(1, std::min(ser.size(), budget / per));
-    const size_t ser_bytes = (sizeof(int2) * ser.size() + 255) & ~(size_t)255;
-    const size_t y_bytes = (sizeof(float2) * t.y_series * chunk + 255) & ~(size_t)255;
-    const size_t a_bytes = (anc_per * chunk + 255) & ~(size_t)255;
-    FRBX_CK(h, ensure(h->ytree, ser_bytes + 2 * (y_bytes + a_bytes)));
-    int2 *d_ser = (int2 *)h->ytree.p;
-    FRBX_CK(h, cudaMemcpyAsync(d_ser, ser.data(), sizeof(int2) * ser.size(), cudaMemcpyHostToDevice, st));
-    // the SBD passes run on one library stream and the MBD passes on the other, so the SBD
-    // pass of chunk i + 1 overlaps the MBD pass of chunk i; chunk parity picks the buffers
-    for (int i = 0; i < 2; ++i)
-      if (!h->tree_st[i]) FRBX_CK(h, cudaStreamCreateWithFlags(&h->tree_st[i], cudaStreamNonBlocking));
-    for (cudaEvent_t &ev : h->tree_ev)
-      if (!ev) FRBX_CK(h, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+      if (T - dkm[(size_t)d] >= 1) r->ser.push_back(make_int2(b, d));
+  // per series: its transformed spectra and the deep anchors of its MBD CTAs
+  const size_t anc_per = sizeof(float2) * frbx::tree_anchor_floats(nlev) * t.n_mb * t.n_tt;
+  const size_t per = sizeof(float2) * t.y_series + anc_per;
+  r->chunk = std::max<size_t>(1, std::min(std::max<size_t>(r->ser.size(), 1), budget / per));
+  r->y_bytes = (sizeof(float2) * t.y_series * r->chunk + 255) & ~(size_t)255;
+  r->a_bytes = (anc_per * r->chunk + 255) & ~(size_t)255;
+}
+
+// Enqueue on st: zero the keys, the chunk passes (SBD passes on one library stream, MBD
+// passes on the other, so the SBD pass of chunk i + 1 overlaps the MBD pass of chunk i;
+// chunk parity picks the buffer set at `bufs`), then the key -> record pass.  d_ser holds
+// r.ser on the device.  With `timing`, every pass is bracketed by events for the stage times.
+int enqueue_tree(frbx_handle *h, const FitArgs &a, const TreeRun &r, const int2 *d_ser, char *bufs, bool timing,
+                 int n_win, const int *win_len, const int *win_off, const int *n_valid, cudaStream_t st) {
+  const frbx::TreeArgs &t = r.t;
+  const size_t n_el = (size_t)r.n_bl * t.n_dm * t.S_tot;
+  if (n_el == 0) return FRBX_OK;
+  FRBX_CK(h, cudaMemsetAsync(a.out, 0, sizeof(frbx_seg) * n_el, st));
+  if (!r.ser.empty()) {
     cudaStream_t sA = h->tree_st[0], sB = h->tree_st[1];
     cudaEvent_t ev_start = h->tree_ev[0], *evA = h->tree_ev + 1, *evB = h->tree_ev + 3;
     FRBX_CK(h, cudaEventRecord(ev_start, st));
     FRBX_CK(h, cudaStreamWaitEvent(sA, ev_start, 0));
     FRBX_CK(h, cudaStreamWaitEvent(sB, ev_start, 0));
-    const int n_chunks = (int)((ser.size() + chunk - 1) / chunk);
-    while ((int)h->tree_kev.size() < 4 * n_chunks) {
-      cudaEvent_t ev = nullptr;
-      FRBX_CK(h, cudaEventCreate(&ev));
-      h->tree_kev.push_back(ev);
+    const int n_chunks = (int)((r.ser.size() + r.chunk - 1) / r.chunk);
+    if (timing) {
+      while ((int)h->tree_kev.size() < 4 * n_chunks) {
+        cudaEvent_t ev = nullptr;
+        FRBX_CK(h, cudaEventCreate(&ev));
+        h->tree_kev.push_back(ev);
+      }
+      h->tree_chunks = n_chunks;
     }
-    h->tree_chunks = n_chunks;
     int ci = 0;
-    for (size_t c0 = 0; c0 < ser.size(); c0 += chunk, ++ci) {
+    for (size_t c0 = 0; c0 < r.ser.size(); c0 += r.chunk, ++ci) {
       const int par = ci & 1;
       frbx::TreeArgs tc = t;
-      char *base = (char *)h->ytree.p + ser_bytes + (size_t)par * (y_bytes + a_bytes);
+      char *base = bufs + (size_t)par * (r.y_bytes + r.a_bytes);
       tc.Y = (float2 *)base;
-      tc.anc_g = (float2 *)(base + y_bytes);
+      tc.anc_g = (float2 *)(base + r.y_bytes);
       tc.series = d_ser + c0;
-      tc.n_s = (int)std::min(chunk, ser.size() - c0);
-      cudaEvent_t *kev = h->tree_kev.data() + 4 * ci;
+      tc.n_s = (int)std::min(r.chunk, r.ser.size() - c0);
+      cudaEvent_t *kev = timing ? h->tree_kev.data() + 4 * ci : nullptr;
       cudaError_t e = cudaSuccess;
-      if (ci >= 2) e = cudaStreamWaitEvent(sA, evB[par], 0);  // the MBD pass two chunks back is done with Y[par]
-      if (e == cudaSuccess) e = cudaEventRecord(kev[0], sA);
+      if (ci >= 2) e = cudaStreamWaitEvent(sA, evB[par], 0);  // the MBD pass two chunks back is done with this set
+      if (e == cudaSuccess && kev) e = cudaEventRecord(kev[0], sA);
       if (e == cudaSuccess) e = frbx::launch_tree_sbd(a, tc, sA, &h->launches);
-      if (e == cudaSuccess) e = cudaEventRecord(kev[1], sA);
+      if (e == cudaSuccess && kev) e = cudaEventRecord(kev[1], sA);
       if (e == cudaSuccess) e = cudaEventRecord(evA[par], sA);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(sB, evA[par], 0);
-      if (e == cudaSuccess) e = cudaEventRecord(kev[2], sB);
-      if (e == cudaSuccess) e = frbx::launch_tree_mbd(tc, full, sB, &h->launches);
-      if (e == cudaSuccess) e = cudaEventRecord(kev[3], sB);
+      if (e == cudaSuccess && kev) e = cudaEventRecord(kev[2], sB);
+      if (e == cudaSuccess) e = frbx::launch_tree_mbd(tc, r.full, sB, &h->launches);
+      if (e == cudaSuccess && kev) e = cudaEventRecord(kev[3], sB);
       if (e == cudaSuccess) e = cudaEventRecord(evB[par], sB);
       if (e == cudaErrorInvalidConfiguration) return fail(h, FRBX_EUNSUPPORTED, "window-tree fit does not fit this shape");
       FRBX_CK(h, e);
@@ -702,10 +711,38 @@ int run_fit_tree(frbx_handle *h, const FitArgs &a, const frbx_params &p, int nle
     FRBX_CK(h, cudaEventRecord(evB[0], sB));
     FRBX_CK(h, cudaStreamWaitEvent(st, evB[0], 0));
   }
-  FRBX_CK(h, frbx::launch_tree_finalize(a.out, (long long)n_el, S_tot, n_dm, n_win, d_tab, d_tab + frbx::kMaxWin,
-                                         d_tab + 3 * frbx::kMaxWin, a.log2Lm, h->Lm, st, &h->launches));
-  (void)p;
+  FRBX_CK(h, frbx::launch_tree_finalize(a.out, (long long)n_el, t.S_tot, t.n_dm, n_win, win_len, win_off, n_valid,
+                                         a.log2Lm, h->Lm, st, &h->launches));
   return FRBX_OK;
+}
+
+// Streams and events of the window-tree fit, made before any stream capture uses them.
+int tree_prepare(frbx_handle *h) {
+  for (int i = 0; i < 2; ++i)
+    if (!h->tree_st[i]) FRBX_CK(h, cudaStreamCreateWithFlags(&h->tree_st[i], cudaStreamNonBlocking));
+  for (cudaEvent_t &ev : h->tree_ev)
+    if (!ev) FRBX_CK(h, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  return FRBX_OK;
+}
+
+// frbx_search's window-tree fit: plan with a budget of a quarter of the free memory (at most
+// 16 GiB per buffer set), size the handle's scratch, upload the series list, enqueue.
+int run_fit_tree(frbx_handle *h, const FitArgs &a, int nlev, const int32_t *windows, int n_win,
+                 const std::vector<int> &dkm, int n_bl, int T, int n_dm, const int *d_tab, int S_tot, cudaStream_t st) {
+  size_t free_b = 0, total_b = 0;
+  FRBX_CK(h, cudaMemGetInfo(&free_b, &total_b));
+  const size_t budget = std::min<size_t>((size_t)16 << 30, (free_b + h->ytree.bytes) / 4);
+  TreeRun r;
+  plan_tree(h, a, nlev, windows, n_win, dkm, n_bl, T, n_dm, d_tab + frbx::kMaxWin, S_tot, budget, &r);
+  int rc = tree_prepare(h);
+  if (rc) return rc;
+  const size_t ser_bytes = (sizeof(int2) * std::max<size_t>(r.ser.size(), 1) + 255) & ~(size_t)255;
+  FRBX_CK(h, ensure(h->ytree, ser_bytes + r.need()));
+  int2 *d_ser = (int2 *)h->ytree.p;
+  if (!r.ser.empty())
+    FRBX_CK(h, cudaMemcpyAsync(d_ser, r.ser.data(), sizeof(int2) * r.ser.size(), cudaMemcpyHostToDevice, st));
+  return enqueue_tree(h, a, r, d_ser, (char *)h->ytree.p + ser_bytes, true, n_win, d_tab, d_tab + frbx::kMaxWin,
+                      d_tab + 3 * frbx::kMaxWin, st);
 }
 
 // Everything after the fit (Eq. 6 and threshold on the device, then the host extraction of
@@ -975,7 +1012,7 @@ extern "C" int frbx_search(frbx_handle *h, const void *vis, int32_t vis_on_devic
   if (p.kernel == 4 && !tree_ok)
     return fail(h, FRBX_EUNSUPPORTED, "window-tree fit needs power-of-two windows <= 64 and Ls, Lm multiples of 32");
   if (p.kernel == 4 || (p.kernel == 0 && tree_ok)) {
-    rc = run_fit_tree(h, a, p, nlev, windows, n_win, dkm, n_bl, T, n_dm, d_tab, L.S_tot, st);
+    rc = run_fit_tree(h, a, nlev, windows, n_win, dkm, n_bl, T, n_dm, d_tab, L.S_tot, st);
     if (rc) return rc;
   } else if (p.kernel == 3 || p.kernel == 5) {
     long long nv = 0;
@@ -1218,7 +1255,7 @@ struct frbx_batch {
   std::string key;
   int captures = 0, replays = 0;
   std::map<std::string, int> tuned_tt;  // setup shape + DM grid + windows -> time tile
-  frbx_handle::Buf desc, tables, series, counters;
+  frbx_handle::Buf desc, tables, series, counters, tree_ser;
   std::vector<int> last_tt;
   double last_fit_ms = 0.0;
   int64_t launches = 0, graph_kernels = 0;
@@ -1264,7 +1301,7 @@ extern "C" void frbx_batch_destroy(frbx_batch *b) {
   if (!b) return;
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
-  for (frbx_handle::Buf *x : {&b->desc, &b->tables, &b->series, &b->counters})
+  for (frbx_handle::Buf *x : {&b->desc, &b->tables, &b->series, &b->counters, &b->tree_ser})
     if (x->p) cudaFree(x->p);
   if (b->e0) cudaEventDestroy(b->e0);
   if (b->e1) cudaEventDestroy(b->e1);
@@ -1303,7 +1340,8 @@ extern "C" int frbx_search_batch(frbx_batch *b, const frbx_scan *scans, int32_t 
   }
   frbx_params p;
   if (params) p = *params; else frbx_default_params(&p);
-  if (p.kernel < 0 || p.kernel > 2) return bfail(b, FRBX_EINVAL, "batched search runs kernels 0, 1 or 2");
+  if (p.kernel < 0 || p.kernel > 4 || p.kernel == 3)
+    return bfail(b, FRBX_EINVAL, "batched search runs kernels 0, 1, 2 or 4");
   // unique setups in order of first appearance
   std::vector<frbx_handle *> setups;
   std::vector<ScanPlan> plan((size_t)n_scans);
@@ -1329,6 +1367,16 @@ extern "C" int frbx_search_batch(frbx_batch *b, const frbx_scan *scans, int32_t 
     int rc = check_params(h, &p, 64, &fa[g]);
     if (!rc) rc = run_shift_table(h, dm, n_dm, &dkm[g], st);
     if (rc) return bfail(b, rc, "setup " + std::to_string(g) + ": " + h->err);
+  }
+  // window-tree fit where it applies (kernel 0) or is asked for (kernel 4)
+  std::vector<int> tree_lev(setups.size(), -1);
+  for (size_t g = 0; g < setups.size(); ++g) {
+    frbx_handle *h = setups[g];
+    int nlev = 0;
+    const bool ok = frbx::tree_supported(h->Ls, h->Lm, h->N, h->J, h->tree_s16, windows, n_win, &nlev);
+    if (p.kernel == 4 && !ok)
+      return bfail(b, FRBX_EUNSUPPORTED, "setup " + std::to_string(g) + ": window-tree fit does not apply");
+    if (ok && (p.kernel == 0 || p.kernel == 4)) tree_lev[g] = nlev;
   }
   // layouts, valid-segment counts, window offsets and series offsets of every scan; one device
   // table: win_len[16] | per scan: win_off[16], n_valid[n_dm][n_win]
@@ -1413,6 +1461,10 @@ extern "C" int frbx_search_batch(frbx_batch *b, const frbx_scan *scans, int32_t 
   std::vector<frbx::BatchScan> desc;
   for (size_t g = 0; g < setups.size(); ++g) {
     frbx_handle *h = setups[g];
+    if (tree_lev[g] >= 0) {  // the window-tree fit has its own fixed tiling
+      b->last_tt[g] = 1024;
+      continue;
+    }
     std::string tkey = std::to_string(h->N) + "x" + std::to_string(h->J) + "/" + std::to_string(h->Ls) + "/" +
                        std::to_string(h->Lm) + "/" + std::to_string(n_dm);
     for (int w = 0; w < n_win; ++w) tkey += "," + std::to_string(windows[w]);
@@ -1467,6 +1519,51 @@ extern "C" int frbx_search_batch(frbx_batch *b, const frbx_scan *scans, int32_t 
   }
   FRBX_BCK(b, cudaMemcpyAsync(d_desc + half, all.data(), sizeof(frbx::BatchScan) * all.size(), cudaMemcpyHostToDevice,
                               st));
+  // window-tree scans: plans, per-setup scratch sized for the largest, series lists uploaded
+  std::vector<TreeRun> truns((size_t)n_scans);
+  std::vector<FitArgs> targs((size_t)n_scans);
+  std::vector<size_t> tser_off((size_t)n_scans, 0);
+  std::vector<size_t> need_h(setups.size(), 0);
+  std::vector<int2> tser_all;
+  size_t n_tree_setups = 0;
+  for (size_t g = 0; g < setups.size(); ++g) n_tree_setups += tree_lev[g] >= 0;
+  int64_t tree_launches = 0;
+  if (n_tree_setups) {
+    size_t free_b = 0, total_b = 0;
+    FRBX_BCK(b, cudaMemGetInfo(&free_b, &total_b));
+    for (int i = 0; i < n_scans; ++i) {
+      const int g = plan[(size_t)i].setup;
+      if (tree_lev[(size_t)g] < 0) continue;
+      frbx_handle *h = setups[(size_t)g];
+      const size_t budget =
+          std::min<size_t>((size_t)16 << 30, (free_b + h->ytree.bytes) / (4 * n_tree_setups));
+      FitArgs a = fit_args(g, 1024);
+      fill_fit_tables(h, &a, (const float2 *)scans[i].vis_dev, scans[i].T, n_dm);
+      a.win_off = d_tab + woff_at[(size_t)i];
+      a.n_valid = d_tab + plan[(size_t)i].nval_off;
+      a.S_tot = plan[(size_t)i].L.S_tot;
+      a.out = d_series + plan[(size_t)i].series_off;
+      targs[(size_t)i] = a;
+      plan_tree(h, a, tree_lev[(size_t)g], windows, n_win, dkm[(size_t)g], scans[i].n_bl, scans[i].T, n_dm,
+                a.win_off, a.S_tot, budget, &truns[(size_t)i]);
+      need_h[(size_t)g] = std::max(need_h[(size_t)g], truns[(size_t)i].need());
+      tser_off[(size_t)i] = tser_all.size();
+      tser_all.insert(tser_all.end(), truns[(size_t)i].ser.begin(), truns[(size_t)i].ser.end());
+      tree_launches += 2 * (int64_t)((truns[(size_t)i].ser.size() + truns[(size_t)i].chunk - 1) / truns[(size_t)i].chunk) + 1;
+    }
+    for (size_t g = 0; g < setups.size(); ++g) {
+      if (tree_lev[g] < 0) continue;
+      frbx_handle *h = setups[g];
+      if (ensure(h->ytree, need_h[g]) != cudaSuccess || tree_prepare(h) != FRBX_OK) {
+        cudaGetLastError();
+        return bfail(b, FRBX_ENOMEM, "setup " + std::to_string(g) + ": window-tree scratch");
+      }
+    }
+    FRBX_BCK(b, ensure(b->tree_ser, sizeof(int2) * std::max<size_t>(tser_all.size(), 1)));
+    if (!tser_all.empty())
+      FRBX_BCK(b, cudaMemcpyAsync(b->tree_ser.p, tser_all.data(), sizeof(int2) * tser_all.size(),
+                                  cudaMemcpyHostToDevice, st));
+  }
   std::string key = std::to_string(n_scans) + ":" + std::to_string(n_dm) + ":" + std::to_string(p.kernel) + ":" +
                     std::to_string((uintptr_t)b->desc.p) + ":" + std::to_string((uintptr_t)b->counters.p);
   for (size_t g = 0; g < setups.size(); ++g) {
@@ -1474,6 +1571,15 @@ extern "C" int frbx_search_batch(frbx_batch *b, const frbx_scan *scans, int32_t 
     const FitArgs a = fit_args((int)g, b->last_tt[g]);
     key += "|" + std::to_string(totals[g]) + "/" + std::to_string(first[g]) + "/";
     key.append(reinterpret_cast<const char *>(&a), sizeof(a));
+  }
+  for (int i = 0; i < n_scans; ++i) {
+    if (tree_lev[(size_t)plan[(size_t)i].setup] < 0) continue;
+    const frbx::TreeArgs &tt = truns[(size_t)i].t;
+    key += "|t" + std::to_string(i) + ":" + std::to_string(truns[(size_t)i].chunk) + ":" +
+           std::to_string((uintptr_t)setups[(size_t)plan[(size_t)i].setup]->ytree.p) + ":" +
+           std::to_string((uintptr_t)b->tree_ser.p) + "/";
+    key.append(reinterpret_cast<const char *>(&tt), sizeof(tt));
+    key.append(reinterpret_cast<const char *>(&targs[(size_t)i]), sizeof(FitArgs));
   }
   if (b->key != key || !b->exec) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
@@ -1488,6 +1594,7 @@ extern "C" int frbx_search_batch(frbx_batch *b, const frbx_scan *scans, int32_t 
     cudaError_t ce = cudaSuccess;
     int64_t graph_launches = 0;
     for (size_t g = 0; g < setups.size() && ce == cudaSuccess; ++g) {
+      if (tree_lev[g] >= 0) continue;
       unsigned int *cnt = d_cnt + 64 * (g + 1);
       ce = cudaMemsetAsync(cnt, 0, sizeof(unsigned int), cs);
       if (ce == cudaSuccess) {
@@ -1496,8 +1603,24 @@ extern "C" int frbx_search_batch(frbx_batch *b, const frbx_scan *scans, int32_t 
                                     cnt, p.kernel, 0, cs, &graph_launches);
       }
     }
+    int trc = FRBX_OK;
+    for (int i = 0; i < n_scans && ce == cudaSuccess && trc == FRBX_OK; ++i) {
+      const int g = plan[(size_t)i].setup;
+      if (tree_lev[(size_t)g] < 0) continue;
+      frbx_handle *h = setups[(size_t)g];
+      trc = enqueue_tree(h, targs[(size_t)i], truns[(size_t)i], (const int2 *)b->tree_ser.p + tser_off[(size_t)i],
+                         (char *)h->ytree.p, false, n_win, d_tab, d_tab + woff_at[(size_t)i],
+                         d_tab + plan[(size_t)i].nval_off, cs);
+      if (trc) b->err = "scan " + std::to_string(i) + ": " + h->err;
+    }
+    graph_launches += tree_launches;
     cudaGraph_t graph = nullptr;
     const cudaError_t ee = cudaStreamEndCapture(cs, &graph);
+    if (trc != FRBX_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return bfail(b, trc, b->err);
+    }
     if (ce != cudaSuccess || ee != cudaSuccess) {
       if (graph) cudaGraphDestroy(graph);
       cudaGetLastError();

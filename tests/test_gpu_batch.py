@@ -62,6 +62,8 @@ def _same(a, b):
 
 @pytest.mark.parametrize("kernel", [0, 1])
 def test_batch_equals_per_scan_search(frbx, kernel):
+    """kernel 0: the VGOS-like scans take the window-tree fit, the small ones the per-segment
+    direct fit, in one captured graph; kernel 1: the persistent per-segment fit everywhere."""
     wls = _scans()
     windows = [1, 2, 4, 8]
     hs = {}
@@ -74,33 +76,54 @@ def test_batch_equals_per_scan_search(frbx, kernel):
         out = b.search(scans, DMS, windows, **kw)
         info = b.info()
         assert info["graph_captures"] == 1 and info["graph_replays"] == 0
-        assert len(info["time_tile"]) == 2 and all(t in (32, 64, 128) for t in info["time_tile"])
+        assert len(info["time_tile"]) == 2 and all(t in (32, 64, 128, 1024) for t in info["time_tile"])
         assert info["fit_ms"] > 0 and info["launches"] >= 2 + 4 * 2
-        for (h, v), o, wl in zip(scans, out, wls):
-            # kernel 0 of the batch is the automatic per-segment fit; frbx_search's automatic
-            # choice on the VGOS-like setup is the window tree, so name the per-segment kernel
-            rk = dict(kw, kernel=2 if (kernel == 0 and wl.name == "vgos") else kernel)
-            ref = h.search(v, DMS, windows, **rk)
-            _same(o, ref)
         # the same shapes in the same buffers: the fit graph is replayed, results unchanged
         again = b.search(scans, DMS, windows, **kw)
         info = b.info()
         assert info["graph_captures"] == 1 and info["graph_replays"] == 1
         for o, o2 in zip(out, again):
             _same(o, o2)
-        # cubes of the same shapes in new buffers: the scan descriptors live in device memory,
-        # so the graph is still replayed, and the results follow the new data
-        vis2 = [v.clone() for v in vis]
-        vis2[1].mul_(2.0)
-        out2 = b.search([(h, v) for (h, _), v in zip(scans, vis2)], DMS, windows, **kw)
+        # new data in the same buffers: replayed, and the results follow the data
+        vis[1].mul_(2.0)
+        out2 = b.search(scans, DMS, windows, **kw)
         info = b.info()
         assert info["graph_captures"] == 1 and info["graph_replays"] == 2
-        np.testing.assert_allclose(out2[1]["series"]["amp"][out[1]["series"]["amp"] >= 0],
-                                   2.0 * out[1]["series"]["amp"][out[1]["series"]["amp"] >= 0], rtol=1e-6)
+        ok = out[1]["series"]["amp"] >= 0
+        np.testing.assert_allclose(out2[1]["series"]["amp"][ok], 2.0 * out[1]["series"]["amp"][ok], rtol=1e-6)
         _same(out2[0], out[0])
         # another DM grid changes the work: re-captured
         b.search(scans, DMS[:7], windows, **kw)
         assert b.info()["graph_captures"] == 2
+    # every scan exactly as frbx_search gives it (same kernels, same arithmetic)
+    for (h, v), o in zip(scans, out2):
+        _same(o, h.search(v, DMS, windows, **kw))
+
+
+def test_batch_window_tree_only(frbx):
+    """kernel 4 (window tree) on VGOS-like scans of three lengths, one spanning several time
+    tiles, against frbx_search with the same kernel; replay with new data."""
+    wls = []
+    for T, off in ((2300, 0), (700, 5), (1200, 9)):
+        wl = synth.make_vgos(T=T, n_bl=2, n_dm=len(DMS), seed_offset=off)
+        wl.dms = DMS.copy()
+        if wls:
+            wl.flags = wls[0].flags.copy()
+            wl.rfi_points = list(wls[0].rfi_points)
+        wls.append(wl)
+    h = frbx.Handle.from_workload(wls[0])
+    vis = [to_dev(synth.generate(wl)) for wl in wls]
+    kw = dict(combos=[0b11], want_series=True, want_events=True, kernel=4)
+    with frbx.Batch() as b:
+        out = b.search([(h, v) for v in vis], DMS, [1, 2, 4, 8, 16], **kw)
+        vis[0].mul_(0.5)  # same buffers, new data: the captured graph is replayed
+        out2 = b.search([(h, v) for v in vis], DMS, [1, 2, 4, 8, 16], **kw)
+        assert b.info()["graph_captures"] == 1 and b.info()["graph_replays"] == 1
+        ok = out[0]["series"]["amp"] >= 0
+        np.testing.assert_allclose(out2[0]["series"]["amp"][ok], 0.5 * out[0]["series"]["amp"][ok], rtol=1e-6)
+        _same(out2[1], out[1])
+        for v, o in zip(vis, out2):
+            _same(o, h.search(v, DMS, [1, 2, 4, 8, 16], **kw))
 
 
 def test_batch_against_oracle(frbx):
