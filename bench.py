@@ -37,9 +37,13 @@ SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12  # 80.5
-# DRAM bytes per fitted segment of the fit kernel, from the ncu capture summarised in
-# profiles/fit_fft_vgos.md (None until a capture of the current kernel exists).
+# DRAM bytes per fitted segment of the per-segment fit kernel (None: no capture of the
+# current kernel).
 FIT_DRAM_BYTES_PER_SEGMENT = None
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_tree_mbd launch per (series, AP) it
+# covers, from an ncu capture of the vgos-profile workload (2.590 + 0.045 GB over
+# 4 x 20000 series-APs); set to None when k_tree_mbd changes
+TREE_MBD_DRAM_BYTES_PER_AP = (2.589522e9 + 0.045097e9) / (4 * 20000)
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 
 
@@ -375,8 +379,11 @@ def main():
         n_l1 = n_ap if 1 in wl.windows else 0
         executed = (n_ap * h.Ls * 5 * h.Lm * math.log2(h.Lm) + (n_seg - n_l1) * 2 * h.Ls * h.Lm
                     + n_seg * 3 * h.Ls * h.Lm)
+        launches_ = max(1, int(stages["tree_chunks"]))
+        traffic = None if TREE_MBD_DRAM_BYTES_PER_AP is None else TREE_MBD_DRAM_BYTES_PER_AP * n_ap / launches_
         roof = {"bound": "alu", "kernel": "k_tree_mbd", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
+                "traffic_note": "bytes per launch, scaled by series-APs from the vgos-profile ncu capture",
                 "peak_note": "FP32 CUDA-core peak 152 SM x 128 lanes x 2 flop x 2070 MHz (derived, not measured)",
                 "work": f"{n_seg} segments x {seg_flop:.0f} flop (2-D FFT count of the method per segment) "
                         f"over {int(stages['tree_chunks'])} launches",
