@@ -35,6 +35,7 @@ namespace frbx {
 
 constexpr int kTreeThreads = 128;
 constexpr int kTreeMaxLev = 6;  // windows up to 64 APs
+constexpr int kSbdBatch = 8;    // SBD pass: cube loads in flight per thread
 
 // Anchors of the window tree: level 1 in registers, the next kTreeSmemAnc levels in shared
 // memory, deeper ones (touched every 16 APs or less often) in a per-CTA slice of device memory.
@@ -75,12 +76,24 @@ __global__ void __launch_bounds__(kTreeThreads, 3)
   const int row4 = Ls * N / 2;  // float4 per AP
   __syncthreads();
   for (int k = k_lo; k < k_hi; ++k) {
-    // Eq. 3 with l = 1: the dedispersed spectrum of AP k, weighted and rotated
+    // Eq. 3 with l = 1: the dedispersed spectrum of AP k, weighted and rotated; kSbdBatch
+    // independent cube loads in flight per thread (the shift-table row stays in L1)
     const size_t row0 = (size_t)sd.x * a.T + k;
-    for (int p = threadIdx.x; p < a.C; p += blockDim.x) {
-      const float2 v = __ldg(a.vis + (row0 + __ldg(dk + p)) * a.C + p);
-      const int n = p / a.J, j = p - n * a.J;
-      X[n * xs + j] = cmul(v, __ldg(a.wrot + p));
+    for (int p0 = threadIdx.x; p0 < a.C; p0 += blockDim.x * kSbdBatch) {
+      float2 v[kSbdBatch];
+#pragma unroll
+      for (int q = 0; q < kSbdBatch; ++q) {
+        const int p = p0 + q * (int)blockDim.x;
+        v[q] = p < a.C ? __ldg(a.vis + (row0 + __ldg(dk + p)) * a.C + p) : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int q = 0; q < kSbdBatch; ++q) {
+        const int p = p0 + q * (int)blockDim.x;
+        if (p < a.C) {
+          const int n = p / a.J, j = p - n * a.J;
+          X[n * xs + j] = cmul(v[q], __ldg(a.wrot + p));
+        }
+      }
     }
     __syncthreads();
     // SBD transform of every channel, task (n, m1); row m = m1 + PS m2 holds the channel slots
