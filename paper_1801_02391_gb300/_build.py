@@ -11,7 +11,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libfrbx.so")
-SOURCES = ["frbx_api.cu", "kernels_fit.cu", "kernels_fft.cu", "kernels_mma.cu", "kernels_misc.cu", "kernels_refine.cu", "kernels_calib.cu", "kernels_tree.cu", "noalloc.cu", "extract.cpp"]
+SOURCES = ["frbx_api.cu", "kernels_fit.cu", "kernels_fft.cu", "kernels_mma.cu", "kernels_misc.cu", "kernels_refine.cu", "kernels_calib.cu", "kernels_tree.cu", "kernels_tree_mma.cu", "noalloc.cu", "extract.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off",
               "-I", os.path.join(ROOT, "include")]

@@ -350,6 +350,48 @@ int frbx_create(const frbx_setup *s, frbx_handle **out) {
     }
     h->b_bytes8 = KA8 * rows * 128;
   }
+  // window-tree tensor-core fit: per block of 32 MBD columns q, the DFT rows (Re G of the 32
+  // q, then Im G) split as W = W_hi + W_lo in BF16, each in its 128-byte swizzled image
+  std::vector<uint16_t> wtree;
+  if (frbx::tree_mma_supported(h->Ls, h->Lm, N, J)) {
+    const int KA = (2 * N + 63) / 64, rows = 64, n_qb = h->Lm / 32, atom = rows * 128;
+    const int wb = 2 * KA * atom;  // bytes per block: hi atoms, then lo atoms
+    wtree.assign((size_t)n_qb * wb / 2, 0);
+    auto bf16 = [](double v) {
+      const float f = (float)v;
+      uint32_t u;
+      std::memcpy(&u, &f, 4);
+      u += 0x7FFFu + ((u >> 16) & 1u);  // round to nearest even
+      return (uint16_t)(u >> 16);
+    };
+    auto bf16f = [](uint16_t b) {
+      const uint32_t u = (uint32_t)b << 16;
+      float f;
+      std::memcpy(&f, &u, 4);
+      return (double)f;
+    };
+    auto put = [&](int qb, int lo, int R, int k, uint16_t v) {
+      const size_t off = (size_t)qb * wb + (size_t)lo * KA * atom + (size_t)(k / 64) * atom + (size_t)(R / 8) * 1024 +
+                         (size_t)(R % 8) * 128 + (size_t)((((k % 64) / 8) ^ (R % 8)) * 16) + (size_t)(k % 8) * 2;
+      wtree[off / 2] = v;
+    };
+    for (int qb = 0; qb < n_qb; ++qb)
+      for (int R = 0; R < rows; ++R) {
+        const int q = qb * 32 + (R % 32);
+        const bool im = R >= 32;
+        for (int n = 0; n < N; ++n) {
+          const long long ex = ((long long)h->g[(size_t)n] * q) % h->Lm;
+          const double th = two_pi * (double)ex / (double)h->Lm;
+          const double vr = im ? -std::sin(th) : std::cos(th), vi = im ? std::cos(th) : std::sin(th);
+          const uint16_t rh = bf16(vr), ih = bf16(vi);
+          put(qb, 0, R, n, rh);
+          put(qb, 0, R, N + n, ih);
+          put(qb, 1, R, n, bf16(vr - bf16f(rh)));
+          put(qb, 1, R, N + n, bf16(vi - bf16f(ih)));
+        }
+      }
+    h->wtree_bytes = wb;
+  }
   cudaError_t e = cudaGetDevice(&h->device);
   if (e == cudaSuccess) e = upload(&h->d_f, h->f);
   if (e == cudaSuccess) e = upload(&h->d_f0, h->f0);
@@ -364,6 +406,7 @@ int frbx_create(const frbx_setup *s, frbx_handle **out) {
   if (e == cudaSuccess) e = upload(&h->d_tree_slot, tree_slot);
   if (e == cudaSuccess && !bimg.empty()) e = upload((uint16_t **)&h->d_bimg, bimg);
   if (e == cudaSuccess && !bimg8.empty()) e = upload((uint8_t **)&h->d_bimg8, bimg8);
+  if (e == cudaSuccess && !wtree.empty()) e = upload((uint16_t **)&h->d_wtree, wtree);
   if (e == cudaSuccess) {
     std::call_once(g_const_once, frbx::set_fft_constants);
     e = cudaGetLastError();
@@ -381,7 +424,8 @@ int frbx_create(const frbx_setup *s, frbx_handle **out) {
 void frbx_destroy(frbx_handle *h) {
   if (!h) return;
   void *ptrs[] = {h->d_f,      h->d_f0,     h->d_wrot, h->d_tw_s, h->d_tw_m,     h->d_g,
-                  h->d_sbd_tw, h->d_mbd_tw, h->d_slot, h->d_bimg, h->d_tree_tw, h->d_tree_slot, h->d_bimg8};
+                  h->d_sbd_tw, h->d_mbd_tw, h->d_slot, h->d_bimg, h->d_tree_tw, h->d_tree_slot, h->d_bimg8,
+                  h->d_wtree};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : h->ev)
@@ -464,7 +508,7 @@ int check_params(frbx_handle *h, const frbx_params *p, int n_bl, FitArgs *a) {
   if (!axis_window(Lm, p->mbd_win_ns, [&](int s) { return ((double)s * 1000.0) / ((double)Lm * dfg); },
                    &a->q_lo, &a->q_len))
     return fail(h, FRBX_EINVAL, "MBD window holds no grid cell");
-  if (p->kernel < 0 || p->kernel > 5) return fail(h, FRBX_EINVAL, "kernel must be 0 to 5");
+  if (p->kernel < 0 || p->kernel > 6) return fail(h, FRBX_EINVAL, "kernel must be 0 to 6");
   if (p->kernel == 3 || p->kernel == 5) {
     if (!h->d_bimg) return fail(h, FRBX_EUNSUPPORTED, "tensor-core fit needs Ls of 64 or 128, 2 Lm >= 32, N <= 64");
     if (a->m_len != Ls || a->q_len != Lm)
@@ -613,7 +657,7 @@ struct TreeRun {
 // Host planning: kernel arguments, series list and chunk size for `budget` bytes per set.
 void plan_tree(const frbx_handle *h, const FitArgs &a, int nlev, const int32_t *windows, int n_win,
                const std::vector<int> &dkm, int n_bl, int T, int n_dm, const int *win_off, int S_tot, size_t budget,
-               TreeRun *r) {
+               bool mma, TreeRun *r) {
   frbx::TreeArgs &t = r->t;
   t = frbx::TreeArgs{};
   r->n_bl = n_bl;
@@ -645,12 +689,25 @@ void plan_tree(const frbx_handle *h, const FitArgs &a, int nlev, const int32_t *
   t.n_ktile = (T + t.k_per_cta - 1) / t.k_per_cta;
   t.y_series = (size_t)T * h->Ls * h->N;
   r->full = a.m_lo == 0 && a.m_len == h->Ls && a.q_lo == 0 && a.q_len == h->Lm;
+  if (mma) {  // tensor-core MBD pass: split A tiles per AP instead of FP32 rows
+    t.mma = 1;
+    t.KA = (2 * h->N + 63) / 64;
+    t.tile_bytes = 2 * t.KA * 128 * 128;
+    t.wimg = (const unsigned char *)h->d_wtree;
+    t.w_bytes = h->wtree_bytes;
+    t.n_qb = h->Lm / 32;
+    t.log2Lm = a.log2Lm;
+    t.err = (int *)h->errflag.p;
+    t.timeout = 2000000000LL;
+    t.yt_series = (size_t)T * t.tile_bytes;
+    t.y_series = t.yt_series / sizeof(float2);
+  }
   r->ser.clear();
   for (int b = 0; b < n_bl; ++b)
     for (int d = 0; d < n_dm; ++d)
       if (T - dkm[(size_t)d] >= 1) r->ser.push_back(make_int2(b, d));
   // per series: its transformed spectra and the deep anchors of its MBD CTAs
-  const size_t anc_per = sizeof(float2) * frbx::tree_anchor_floats(nlev) * t.n_mb * t.n_tt;
+  const size_t anc_per = mma ? 0 : sizeof(float2) * frbx::tree_anchor_floats(nlev) * t.n_mb * t.n_tt;
   const size_t per = sizeof(float2) * t.y_series + anc_per;
   r->chunk = std::max<size_t>(1, std::min(std::max<size_t>(r->ser.size(), 1), budget / per));
   r->y_bytes = (sizeof(float2) * t.y_series * r->chunk + 255) & ~(size_t)255;
@@ -688,6 +745,7 @@ int enqueue_tree(frbx_handle *h, const FitArgs &a, const TreeRun &r, const int2 
       frbx::TreeArgs tc = t;
       char *base = bufs + (size_t)par * (r.y_bytes + r.a_bytes);
       tc.Y = (float2 *)base;
+      tc.Yt = (const unsigned char *)base;
       tc.anc_g = (float2 *)(base + r.y_bytes);
       tc.series = d_ser + c0;
       tc.n_s = (int)std::min(r.chunk, r.ser.size() - c0);
@@ -700,7 +758,8 @@ int enqueue_tree(frbx_handle *h, const FitArgs &a, const TreeRun &r, const int2 
       if (e == cudaSuccess) e = cudaEventRecord(evA[par], sA);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(sB, evA[par], 0);
       if (e == cudaSuccess && kev) e = cudaEventRecord(kev[2], sB);
-      if (e == cudaSuccess) e = frbx::launch_tree_mbd(tc, r.full, sB, &h->launches);
+      if (e == cudaSuccess)
+        e = t.mma ? frbx::launch_tree_mma(tc, sB, &h->launches) : frbx::launch_tree_mbd(tc, r.full, sB, &h->launches);
       if (e == cudaSuccess && kev) e = cudaEventRecord(kev[3], sB);
       if (e == cudaSuccess) e = cudaEventRecord(evB[par], sB);
       if (e == cudaErrorInvalidConfiguration) return fail(h, FRBX_EUNSUPPORTED, "window-tree fit does not fit this shape");
@@ -727,13 +786,17 @@ int tree_prepare(frbx_handle *h) {
 
 // frbx_search's window-tree fit: plan with a budget of a quarter of the free memory (at most
 // 16 GiB per buffer set), size the handle's scratch, upload the series list, enqueue.
-int run_fit_tree(frbx_handle *h, const FitArgs &a, int nlev, const int32_t *windows, int n_win,
+int run_fit_tree(frbx_handle *h, const FitArgs &a, int nlev, bool mma, const int32_t *windows, int n_win,
                  const std::vector<int> &dkm, int n_bl, int T, int n_dm, const int *d_tab, int S_tot, cudaStream_t st) {
   size_t free_b = 0, total_b = 0;
   FRBX_CK(h, cudaMemGetInfo(&free_b, &total_b));
   const size_t budget = std::min<size_t>((size_t)16 << 30, (free_b + h->ytree.bytes) / 4);
+  if (mma) {
+    FRBX_CK(h, ensure(h->errflag, sizeof(int)));
+    FRBX_CK(h, cudaMemsetAsync(h->errflag.p, 0, sizeof(int), st));
+  }
   TreeRun r;
-  plan_tree(h, a, nlev, windows, n_win, dkm, n_bl, T, n_dm, d_tab + frbx::kMaxWin, S_tot, budget, &r);
+  plan_tree(h, a, nlev, windows, n_win, dkm, n_bl, T, n_dm, d_tab + frbx::kMaxWin, S_tot, budget, mma, &r);
   int rc = tree_prepare(h);
   if (rc) return rc;
   const size_t ser_bytes = (sizeof(int2) * std::max<size_t>(r.ser.size(), 1) + 255) & ~(size_t)255;
@@ -741,8 +804,14 @@ int run_fit_tree(frbx_handle *h, const FitArgs &a, int nlev, const int32_t *wind
   int2 *d_ser = (int2 *)h->ytree.p;
   if (!r.ser.empty())
     FRBX_CK(h, cudaMemcpyAsync(d_ser, r.ser.data(), sizeof(int2) * r.ser.size(), cudaMemcpyHostToDevice, st));
-  return enqueue_tree(h, a, r, d_ser, (char *)h->ytree.p + ser_bytes, true, n_win, d_tab, d_tab + frbx::kMaxWin,
-                      d_tab + 3 * frbx::kMaxWin, st);
+  rc = enqueue_tree(h, a, r, d_ser, (char *)h->ytree.p + ser_bytes, true, n_win, d_tab, d_tab + frbx::kMaxWin,
+                    d_tab + 3 * frbx::kMaxWin, st);
+  if (rc || !mma) return rc;
+  int flag = 0;
+  FRBX_CK(h, cudaMemcpyAsync(&flag, h->errflag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  FRBX_CK(h, cudaStreamSynchronize(st));
+  if (flag) return fail(h, FRBX_ETIMEOUT, "window-tree tensor-core fit: a bounded wait gave up");
+  return FRBX_OK;
 }
 
 // Everything after the fit (Eq. 6 and threshold on the device, then the host extraction of
@@ -914,7 +983,7 @@ extern "C" int frbx_fit_segments(frbx_handle *h, const void *vis, int32_t vis_on
   FRBX_CK(h, ensure(h->seglist, sizeof(int32_t) * 4 * (size_t)n_seg));
   FRBX_CK(h, ensure(h->series, sizeof(frbx_seg) * (size_t)n_seg));
   FRBX_CK(h, cudaMemcpyAsync(h->seglist.p, segs, sizeof(int32_t) * 4 * (size_t)n_seg, cudaMemcpyHostToDevice, st));
-  if (p.kernel == 4) p.kernel = 0;  // explicit segment lists have no window structure to exploit
+  if (p.kernel == 4 || p.kernel == 6) p.kernel = 0;  // explicit segment lists have no window structure to exploit
   fill_fit_tables(h, &a, dvis, T, n_dm);
   a.seg = (const int *)h->seglist.p;
   a.n_seg = n_seg;
@@ -1009,10 +1078,15 @@ extern "C" int frbx_search(frbx_handle *h, const void *vis, int32_t vis_on_devic
   FRBX_CK(h, cudaEventRecord(h->ev[2], st));
   int nlev = 0;
   const bool tree_ok = frbx::tree_supported(h->Ls, h->Lm, h->N, h->J, h->tree_s16, windows, n_win, &nlev);
-  if (p.kernel == 4 && !tree_ok)
-    return fail(h, FRBX_EUNSUPPORTED, "window-tree fit needs power-of-two windows <= 64 and Ls, Lm multiples of 32");
-  if (p.kernel == 4 || (p.kernel == 0 && tree_ok)) {
-    rc = run_fit_tree(h, a, nlev, windows, n_win, dkm, n_bl, T, n_dm, d_tab, L.S_tot, st);
+  const bool full_grid = a.m_lo == 0 && a.m_len == h->Ls && a.q_lo == 0 && a.q_len == h->Lm;
+  const bool tree_tc = tree_ok && full_grid && h->d_wtree && frbx::tree_mma_supported(h->Ls, h->Lm, h->N, h->J);
+  if ((p.kernel == 4 && !tree_ok) || (p.kernel == 6 && !tree_tc))
+    return fail(h, FRBX_EUNSUPPORTED,
+                "window-tree fit needs power-of-two windows <= 64 and Ls, Lm multiples of 32 (tensor cores: Ls 128, "
+                "2N <= 128, no delay windows)");
+  if (p.kernel == 4 || p.kernel == 6 || (p.kernel == 0 && tree_ok)) {
+    const bool mma = p.kernel == 6 || (p.kernel == 0 && tree_tc);
+    rc = run_fit_tree(h, a, nlev, mma, windows, n_win, dkm, n_bl, T, n_dm, d_tab, L.S_tot, st);
     if (rc) return rc;
   } else if (p.kernel == 3 || p.kernel == 5) {
     long long nv = 0;
@@ -1340,8 +1414,8 @@ extern "C" int frbx_search_batch(frbx_batch *b, const frbx_scan *scans, int32_t 
   }
   frbx_params p;
   if (params) p = *params; else frbx_default_params(&p);
-  if (p.kernel < 0 || p.kernel > 4 || p.kernel == 3)
-    return bfail(b, FRBX_EINVAL, "batched search runs kernels 0, 1, 2 or 4");
+  if (p.kernel < 0 || p.kernel > 6 || p.kernel == 3 || p.kernel == 5)
+    return bfail(b, FRBX_EINVAL, "batched search runs kernels 0, 1, 2, 4 or 6");
   // unique setups in order of first appearance
   std::vector<frbx_handle *> setups;
   std::vector<ScanPlan> plan((size_t)n_scans);
@@ -1370,13 +1444,20 @@ extern "C" int frbx_search_batch(frbx_batch *b, const frbx_scan *scans, int32_t 
   }
   // window-tree fit where it applies (kernel 0) or is asked for (kernel 4)
   std::vector<int> tree_lev(setups.size(), -1);
+  std::vector<char> tree_tc(setups.size(), 0);
   for (size_t g = 0; g < setups.size(); ++g) {
     frbx_handle *h = setups[g];
     int nlev = 0;
     const bool ok = frbx::tree_supported(h->Ls, h->Lm, h->N, h->J, h->tree_s16, windows, n_win, &nlev);
-    if (p.kernel == 4 && !ok)
+    const FitArgs &ag = fa[g];
+    const bool tc_ok = ok && h->d_wtree && frbx::tree_mma_supported(h->Ls, h->Lm, h->N, h->J) && ag.m_lo == 0 &&
+                       ag.m_len == h->Ls && ag.q_lo == 0 && ag.q_len == h->Lm;
+    if ((p.kernel == 4 && !ok) || (p.kernel == 6 && !tc_ok))
       return bfail(b, FRBX_EUNSUPPORTED, "setup " + std::to_string(g) + ": window-tree fit does not apply");
-    if (ok && (p.kernel == 0 || p.kernel == 4)) tree_lev[g] = nlev;
+    if (ok && (p.kernel == 0 || p.kernel == 4 || p.kernel == 6)) {
+      tree_lev[g] = nlev;
+      tree_tc[g] = (p.kernel == 6 || (p.kernel == 0 && tc_ok)) ? 1 : 0;
+    }
   }
   // layouts, valid-segment counts, window offsets and series offsets of every scan; one device
   // table: win_len[16] | per scan: win_off[16], n_valid[n_dm][n_win]
@@ -1529,6 +1610,8 @@ extern "C" int frbx_search_batch(frbx_batch *b, const frbx_scan *scans, int32_t 
   for (size_t g = 0; g < setups.size(); ++g) n_tree_setups += tree_lev[g] >= 0;
   int64_t tree_launches = 0;
   if (n_tree_setups) {
+    for (size_t g = 0; g < setups.size(); ++g)
+      if (tree_lev[g] >= 0) FRBX_BCK(b, ensure(setups[g]->errflag, sizeof(int)));
     size_t free_b = 0, total_b = 0;
     FRBX_BCK(b, cudaMemGetInfo(&free_b, &total_b));
     for (int i = 0; i < n_scans; ++i) {
@@ -1545,7 +1628,7 @@ extern "C" int frbx_search_batch(frbx_batch *b, const frbx_scan *scans, int32_t 
       a.out = d_series + plan[(size_t)i].series_off;
       targs[(size_t)i] = a;
       plan_tree(h, a, tree_lev[(size_t)g], windows, n_win, dkm[(size_t)g], scans[i].n_bl, scans[i].T, n_dm,
-                a.win_off, a.S_tot, budget, &truns[(size_t)i]);
+                a.win_off, a.S_tot, budget, tree_tc[(size_t)g] != 0, &truns[(size_t)i]);
       need_h[(size_t)g] = std::max(need_h[(size_t)g], truns[(size_t)i].need());
       tser_off[(size_t)i] = tser_all.size();
       tser_all.insert(tser_all.end(), truns[(size_t)i].ser.begin(), truns[(size_t)i].ser.end());
@@ -1554,7 +1637,8 @@ extern "C" int frbx_search_batch(frbx_batch *b, const frbx_scan *scans, int32_t 
     for (size_t g = 0; g < setups.size(); ++g) {
       if (tree_lev[g] < 0) continue;
       frbx_handle *h = setups[g];
-      if (ensure(h->ytree, need_h[g]) != cudaSuccess || tree_prepare(h) != FRBX_OK) {
+      if (ensure(h->errflag, sizeof(int)) != cudaSuccess || ensure(h->ytree, need_h[g]) != cudaSuccess ||
+          tree_prepare(h) != FRBX_OK) {
         cudaGetLastError();
         return bfail(b, FRBX_ENOMEM, "setup " + std::to_string(g) + ": window-tree scratch");
       }
@@ -1604,6 +1688,8 @@ extern "C" int frbx_search_batch(frbx_batch *b, const frbx_scan *scans, int32_t 
       }
     }
     int trc = FRBX_OK;
+    for (size_t g = 0; g < setups.size() && ce == cudaSuccess; ++g)
+      if (tree_lev[g] >= 0) ce = cudaMemsetAsync(setups[g]->errflag.p, 0, sizeof(int), cs);
     for (int i = 0; i < n_scans && ce == cudaSuccess && trc == FRBX_OK; ++i) {
       const int g = plan[(size_t)i].setup;
       if (tree_lev[(size_t)g] < 0) continue;
@@ -1651,6 +1737,12 @@ extern "C" int frbx_search_batch(frbx_batch *b, const frbx_scan *scans, int32_t 
     b->last_fit_ms = ms;
   }
   b->launches += b->graph_kernels;
+  for (size_t g = 0; g < setups.size(); ++g) {
+    if (!tree_tc[g]) continue;
+    int flag = 0;
+    FRBX_BCK(b, cudaMemcpy(&flag, setups[g]->errflag.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) return bfail(b, FRBX_ETIMEOUT, "setup " + std::to_string(g) + ": a bounded wait of the fit gave up");
+  }
 
   // per scan: Eq. 6 and threshold on the device, then the host extraction, as in frbx_search;
   // the scan's window tables go to the head of its setup's small buffer in that layout

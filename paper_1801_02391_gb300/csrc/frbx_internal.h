@@ -150,7 +150,21 @@ struct TreeArgs {
   const int *slot_of;      // [N] slot of channel n in a Y row: (g_n mod 16) + 16 rank
   const float2 *tw;        // [NS/2][PM][2][2] MBD twiddles folded with the first DIF stage (0: empty)
   float2 *anc_g;           // deep window-tree anchors, one slice per MBD CTA
+  // tensor-core MBD pass (3-term split BF16): Y as per-AP A tiles, W per block of 32 q
+  int mma;                 // 1: the SBD pass writes split tiles and the MBD pass is k_tree_mma
+  const unsigned char *Yt; // split tiles [n_s][T][tile_bytes] (aliases Y)
+  size_t yt_series;        // bytes per series in Yt
+  int KA;                  // 64-wide K atoms per tile row (K = 2N)
+  int tile_bytes;          // one AP: hi tile then lo tile, 2 KA 16 KB
+  const unsigned char *wimg;  // [Lm/32][hi | lo][KA][64 rows x 128 B]
+  int w_bytes;             // per block of 32 q: 2 KA 8 KB
+  int n_qb;                // Lm / 32
+  int log2Lm;
+  int *err;                // set to FRBX_ETIMEOUT when a bounded wait of k_tree_mma gives up
+  long long timeout;       // clock cycles per wait
 };
+bool tree_mma_supported(int Ls, int Lm, int N, int J);
+cudaError_t launch_tree_mma(const TreeArgs &t, cudaStream_t st, int64_t *launches);
 bool tree_supported(int Ls, int Lm, int N, int J, int s16, const int *windows, int n_win, int *nlev);
 size_t tree_anchor_floats(int nlev);  // float2 per MBD CTA in TreeArgs::anc_g
 cudaError_t launch_tree_sbd(const FitArgs &a, const TreeArgs &t, cudaStream_t st, int64_t *launches);
@@ -231,6 +245,8 @@ struct frbx_handle {
   int tree_chunks = 0;               // chunks of the last window-tree fit (0: another kernel ran)
   void *d_bimg = nullptr;  // BF16 DFT matrix image for the tensor-core fit (if supported)
   void *d_bimg8 = nullptr;  // the same matrix in E4M3
+  void *d_wtree = nullptr;  // window-tree tensor-core fit: split-BF16 DFT blocks of 32 q
+  int wtree_bytes = 0;      // per block
   int b_bytes = 0, b_bytes8 = 0, b_atom_bytes = 0, KA = 0, NC = 0;
   int *d_g = nullptr, *d_slot = nullptr;
   // scratch, grown on demand

@@ -28,8 +28,11 @@
 //              Each emitted segment's maximum over the block's cells is reduced in the CTA and
 //              merged across blocks by a 64-bit atomicMax on (|G|^2 bits, ~cell index) in the
 //              series buffer, which k_tree_finalize turns into frbx_seg records.
+#include <cuda_bf16.h>
+
 #include "fit_common.cuh"
 #include "fft32.cuh"
+#include "tc_common.cuh"
 
 namespace frbx {
 
@@ -53,15 +56,23 @@ __host__ __device__ inline size_t tree_smem_bytes(int NS, int PM, int RB, int nl
 }
 
 // ----------------------------------------------------------------------------- SBD pass
+// kSplit: instead of FP32 rows, each AP's output is the tensor-core A operand of k_tree_mma in
+// its shared-memory image: A_hi = bf16(Y) then A_lo = bf16(Y - A_hi), 128 rows x K = 2N
+// (Re Y of the channels, then Im Y), 128-byte swizzled K atoms.
+template <bool kSplit>
 __global__ void __launch_bounds__(kTreeThreads, 3)
     k_tree_sbd(const __grid_constant__ FitArgs a, const __grid_constant__ TreeArgs t) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int N = a.N, Ls = a.Ls, PS = Ls >> 5, lps = __ffs(PS) - 1;
   const int JP = a.J1 * 32, xs = JP + 1;
-  float2 *Ys = reinterpret_cast<float2 *>(smem);  // [Ls][N]
-  float2 *X = Ys + Ls * N;                        // [N][xs]
-  float2 *stw = X + N * xs;                       // [PS][xs]
+  const int stage = kSplit ? t.tile_bytes : (int)sizeof(float2) * Ls * N;  // one AP of output
+  float2 *Ys = reinterpret_cast<float2 *>(smem);                          // [Ls][N] or the tiles
+  unsigned char *Yb = smem;
+  float2 *X = reinterpret_cast<float2 *>(smem + stage);  // [N][xs]
+  float2 *stw = X + N * xs;                              // [PS][xs]
   for (int i = threadIdx.x; i < N * xs; i += blockDim.x) X[i] = make_float2(0.f, 0.f);
+  if (kSplit)  // K columns beyond 2N stay zero
+    for (int i = threadIdx.x; i < stage / 16; i += blockDim.x) reinterpret_cast<uint4 *>(Yb)[i] = make_uint4(0, 0, 0, 0);
   for (int i = threadIdx.x; i < PS * JP; i += blockDim.x) {
     const int r = i / JP, c = i - r * JP;
     stw[r * xs + c] = a.sbd_tw[i];
@@ -72,8 +83,9 @@ __global__ void __launch_bounds__(kTreeThreads, 3)
   const int kd = a.T - t.dk_max[sd.y];
   const int k_lo = tile * t.k_per_cta, k_hi = min(kd, k_lo + t.k_per_cta);
   const int *dk = a.dk + (size_t)sd.y * a.C;
-  float4 *Yout = reinterpret_cast<float4 *>(t.Y + (size_t)s * t.y_series);
-  const int row4 = Ls * N / 2;  // float4 per AP
+  float4 *Yout = kSplit ? reinterpret_cast<float4 *>(const_cast<unsigned char *>(t.Yt) + (size_t)s * t.yt_series)
+                        : reinterpret_cast<float4 *>(t.Y + (size_t)s * t.y_series);
+  const int row4 = stage / 16;  // float4 per AP
   __syncthreads();
   for (int k = k_lo; k < k_hi; ++k) {
     // Eq. 3 with l = 1: the dedispersed spectrum of AP k, weighted and rotated; kSbdBatch
@@ -109,11 +121,27 @@ __global__ void __launch_bounds__(kTreeThreads, 3)
         for (int j2 = 0; j2 < 32; ++j2) A[j2] = cfma(A[j2], xr[j1 * 32 + j2], wr[j1 * 32 + j2]);
       }
       fft32_dif(A);
+      if (kSplit) {
+        const int half = t.tile_bytes / 2;
 #pragma unroll
-      for (int i = 0; i < 32; ++i) Ys[(m1 + PS * bitrev5(i)) * N + n] = A[i];
+        for (int i = 0; i < 32; ++i) {
+          const int row = m1 + PS * bitrev5(i);
+          const __nv_bfloat16 rh = __float2bfloat16_rn(A[i].x), ih = __float2bfloat16_rn(A[i].y);
+          const __nv_bfloat16 rl = __float2bfloat16_rn(A[i].x - __bfloat162float(rh));
+          const __nv_bfloat16 il = __float2bfloat16_rn(A[i].y - __bfloat162float(ih));
+          const uint32_t orr = tc::a_offset(row, n), oi = tc::a_offset(row, N + n);
+          *reinterpret_cast<__nv_bfloat16 *>(Yb + orr) = rh;
+          *reinterpret_cast<__nv_bfloat16 *>(Yb + oi) = ih;
+          *reinterpret_cast<__nv_bfloat16 *>(Yb + half + orr) = rl;
+          *reinterpret_cast<__nv_bfloat16 *>(Yb + half + oi) = il;
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) Ys[(m1 + PS * bitrev5(i)) * N + n] = A[i];
+      }
     }
     __syncthreads();
-    const float4 *src = reinterpret_cast<const float4 *>(Ys);
+    const float4 *src = reinterpret_cast<const float4 *>(Yb);
     float4 *dst = Yout + (size_t)k * row4;
     for (int i = threadIdx.x; i < row4; i += blockDim.x) dst[i] = src[i];
     __syncthreads();
@@ -352,19 +380,21 @@ bool tree_supported(int Ls, int Lm, int N, int J, int s16, const int *windows, i
 
 size_t tree_anchor_floats(int nlev) { return (size_t)tree_global_anchors(nlev) * 16 * kTreeThreads; }
 
-size_t tree_sbd_smem(const FitArgs &a) {
+size_t tree_sbd_smem(const FitArgs &a, const TreeArgs &t) {
   const int JP = a.J1 * 32;
-  return sizeof(float2) * ((size_t)a.Ls * a.N + (size_t)a.N * (JP + 1) + (size_t)(a.Ls / 32) * (JP + 1));
+  const size_t stage = t.mma ? (size_t)t.tile_bytes : sizeof(float2) * (size_t)a.Ls * a.N;
+  return stage + sizeof(float2) * ((size_t)a.N * (JP + 1) + (size_t)(a.Ls / 32) * (JP + 1));
 }
 
 cudaError_t launch_tree_sbd(const FitArgs &a, const TreeArgs &t, cudaStream_t st, int64_t *launches) {
-  const size_t smem = tree_sbd_smem(a);
+  const size_t smem = tree_sbd_smem(a, t);
   if (smem > max_smem_optin()) return cudaErrorInvalidConfiguration;
   const long long nb = (long long)t.n_s * t.n_ktile;
   if (nb <= 0) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_tree_sbd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = t.mma ? k_tree_sbd<true> : k_tree_sbd<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_tree_sbd<<<(unsigned)nb, kTreeThreads, smem, st>>>(a, t);
+  kern<<<(unsigned)nb, kTreeThreads, smem, st>>>(a, t);
   ++*launches;
   return cudaGetLastError();
 }

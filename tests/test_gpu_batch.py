@@ -100,9 +100,11 @@ def test_batch_equals_per_scan_search(frbx, kernel):
         _same(o, h.search(v, DMS, windows, **kw))
 
 
-def test_batch_window_tree_only(frbx):
-    """kernel 4 (window tree) on VGOS-like scans of three lengths, one spanning several time
-    tiles, against frbx_search with the same kernel; replay with new data."""
+@pytest.mark.parametrize("kernel", [4, 6])
+def test_batch_window_tree_only(frbx, kernel):
+    """Window-tree kernels (4: CUDA cores, 6: tensor cores) on VGOS-like scans of three
+    lengths, one spanning several time tiles, against frbx_search with the same kernel;
+    replay with new data."""
     wls = []
     for T, off in ((2300, 0), (700, 5), (1200, 9)):
         wl = synth.make_vgos(T=T, n_bl=2, n_dm=len(DMS), seed_offset=off)
@@ -113,7 +115,7 @@ def test_batch_window_tree_only(frbx):
         wls.append(wl)
     h = frbx.Handle.from_workload(wls[0])
     vis = [to_dev(synth.generate(wl)) for wl in wls]
-    kw = dict(combos=[0b11], want_series=True, want_events=True, kernel=4)
+    kw = dict(combos=[0b11], want_series=True, want_events=True, kernel=kernel)
     with frbx.Batch() as b:
         out = b.search([(h, v) for v in vis], DMS, [1, 2, 4, 8, 16], **kw)
         vis[0].mul_(0.5)  # same buffers, new data: the captured graph is replayed

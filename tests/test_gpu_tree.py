@@ -1,7 +1,9 @@
-"""Window-tree fit (kernel 4, the automatic choice where it applies): every window of a
-power-of-two set is built from one-AP delay-resolution matrices by the additivity of
-Sec. 5.1, G_{k0,l} + G_{k0+l,l} = G_{k0,2l}.  Compared with the FP64 oracle element by
-element, on several grid shapes (Lm/32 = 16, 8 and 1 MBD column classes), window sets with
+"""Window-tree fits: every window of a power-of-two set is built from one-AP delay-resolution
+matrices by the additivity of Sec. 5.1, G_{k0,l} + G_{k0+l,l} = G_{k0,2l}.  Kernel 4 runs the
+MBD transform on the CUDA cores in FP32; kernel 6 (the automatic choice where it applies)
+runs it on the tensor cores as a three-term split-BF16 GEMM with FP32 accumulation (about
+1e-5 relative).  Both are compared with the FP64 oracle element by element, to the FP32
+tolerance, on several grid shapes (Lm/32 = 16, 8 and 1 MBD column classes), window sets with
 and without gaps, more than one time tile, delay windows and scans that DM trials sweep past."""
 import numpy as np
 import pytest
@@ -52,10 +54,11 @@ def _run(frbx, wl, windows, combos=(3,), kernel=4, **kw):
     return h, out
 
 
+@pytest.mark.parametrize("kernel", [4, 6])
 @pytest.mark.parametrize("windows", [[1, 2, 4, 8, 16, 32], [2, 4, 8, 16], [1, 4, 16], [8], [64, 1]])
-def test_tree_search_matches_oracle(frbx, windows):
+def test_tree_search_matches_oracle(frbx, windows, kernel):
     # T = 1300 spans two time tiles of 1024 APs; DM 1700 leaves about 400 APs of valid sweep
-    _run(frbx, _vgos(), windows)
+    _run(frbx, _vgos(), windows, kernel=kernel)
 
 
 def test_tree_is_the_automatic_choice(frbx):
@@ -64,12 +67,17 @@ def test_tree_is_the_automatic_choice(frbx):
     vis = to_dev(synth.generate(wl))
     h = frbx.Handle.from_workload(wl)
     auto = h.search(vis, wl.dms, wl.windows, want_series=True)
-    tree = h.search(vis, wl.dms, wl.windows, want_series=True, kernel=4)
-    assert np.array_equal(auto["series"], tree["series"])
+    assert h.stage_times()["tree_chunks"] > 0
+    tc = h.search(vis, wl.dms, wl.windows, want_series=True, kernel=6)
+    assert np.array_equal(auto["series"], tc["series"])
     seg = h.search(vis, wl.dms, wl.windows, want_series=True, kernel=2)
     ok = seg["series"]["amp"] >= 0
-    assert np.array_equal(ok, tree["series"]["amp"] >= 0)
-    np.testing.assert_allclose(tree["series"]["amp"][ok], seg["series"]["amp"][ok], rtol=1e-4)
+    for k in (4, 6):
+        tree = h.search(vis, wl.dms, wl.windows, want_series=True, kernel=k)
+        assert np.array_equal(ok, tree["series"]["amp"] >= 0)
+        rel = np.abs(tree["series"]["amp"][ok] - seg["series"]["amp"][ok]) / seg["series"]["amp"][ok]
+        print(f"kernel {k} vs per-segment FFT: max rel {rel.max():.2e}, median {np.median(rel):.2e}")
+        assert rel.max() <= 1e-4
 
 
 def test_tree_two_band_grid(frbx):
@@ -80,6 +88,7 @@ def test_tree_two_band_grid(frbx):
     wl.phase0 = np.array([0.3, 2.0])
     wl.pulses = [synth.Pulse(dm=300.0, t0_bin=200, width=3, snr=25.0)]
     _run(frbx, wl, [2, 4, 8, 16], combos=(3, 1))
+    _run(frbx, wl, [2, 4, 8, 16], combos=(3, 1), kernel=6)
 
 
 def test_tree_single_column_class_grid(frbx):
@@ -122,8 +131,13 @@ def test_tree_scan_swept_past(frbx):
 def test_tree_rejects_other_windows(frbx):
     wl = _vgos(T=300, n_bl=1, dms=(0.0,))
     h = frbx.Handle.from_workload(wl)
+    for k in (4, 6):
+        with pytest.raises(frbx.FrbxError) as e:
+            h.search(to_dev(synth.generate(wl)), wl.dms, [3, 6], kernel=k)
+        assert e.value.code == frbx.FRBX_EUNSUPPORTED
+    # the tensor-core tree searches the whole grid only
     with pytest.raises(frbx.FrbxError) as e:
-        h.search(to_dev(synth.generate(wl)), wl.dms, [3, 6], kernel=4)
+        h.search(to_dev(synth.generate(wl)), wl.dms, [1, 2], kernel=6, sbd_win_ns=(-50.0, 50.0))
     assert e.value.code == frbx.FRBX_EUNSUPPORTED
     # the automatic choice falls back to the per-segment fit for such windows
     out = h.search(to_dev(synth.generate(wl)), wl.dms, [3, 6], want_series=True)
