@@ -14,8 +14,8 @@
 //   warp 9 (one lane) copies each AP's split A tiles (written by k_tree_sbd in their
 //          shared-memory image) into a ring with cp.async.bulk;
 //   warp 8 allocates tensor memory and one lane issues the 3 x K/16 MMAs of an AP into one
-//          of two accumulator slots;
-//   warps 0-7 (row quarter w % 4, q half w / 4) read G_1(k) and, from the other slot,
+//          of three accumulator slots (so it runs up to two APs ahead);
+//   warps 0-7 (row quarter w % 4, q half w / 4) read G_1(k) and, from the previous slot,
 //          G_1(k - 1), walk their 16 cells through the window tree (deeper anchors held in
 //          tensor memory), and reduce every emitted segment's maximum, merged across blocks
 //          by a 64-bit atomicMax as in k_tree_mbd.
@@ -37,7 +37,8 @@ constexpr int kTmEpiWarps = 8;
 constexpr int kTmMmaWarp = 8, kTmLoadWarp = 9;
 constexpr int kTmThreads = 320;
 constexpr int kTmBarEpi = 1;                // named barrier of the epilogue warps
-constexpr int kTmTmemCols = 512;            // slots 0, 1 at 0, 64; anchors at 128 + 64 j
+constexpr int kTmSlots = 3;                 // accumulator slots: the MMA runs up to two APs ahead
+constexpr int kTmTmemCols = 512;            // slots at 0, 64, 128; anchors at 192 + 64 j
 constexpr int kTmMaxLev = 6;
 constexpr int kTmWAtom = kTmCols * 128;     // one 64-wide K atom of a W block (8 KB)
 
@@ -60,7 +61,6 @@ __device__ __forceinline__ void tm_st16(uint32_t taddr, const float (&v)[16]) {
                  "r"(__float_as_uint(v[15]))
                : "memory");
 }
-__device__ __forceinline__ void named_sync_epi() { tc::named_sync(kTmBarEpi, kTmEpiWarps * 32); }
 __device__ __forceinline__ bool named_sync_or_epi(bool p) { return tc::named_sync_or(kTmBarEpi, kTmEpiWarps * 32, p); }
 __device__ __forceinline__ void tm_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
@@ -70,16 +70,18 @@ __device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sy
 __global__ void __launch_bounds__(kTmThreads, 1) k_tree_mma(const __grid_constant__ TreeArgs t) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ uint64_t bar_afull[kTmABufs], bar_aempty[kTmABufs], bar_accfull[2], bar_accempty[2], bar_drain;
+  __shared__ uint64_t bar_afull[kTmABufs], bar_aempty[kTmABufs], bar_accfull[kTmSlots], bar_accempty[kTmSlots],
+      bar_drain;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   __shared__ uint2 red[2][kTmMaxLev + 1][kTmEpiWarps];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // MBD column blocks vary fastest, so the CTAs sharing one series' A tiles run together (L2)
   int item = blockIdx.x;
-  const int tt = item % t.n_tt;
-  item /= t.n_tt;
-  const int qb = item % t.n_qb, s = item / t.n_qb;
+  const int qb = item % t.n_qb;
+  item /= t.n_qb;
+  const int tt = item % t.n_tt, s = item / t.n_tt;
   const int2 sd = t.series[s];
   const int kd = t.T - t.dk_max[sd.y];
   const int kb = tt * t.TT;
@@ -99,7 +101,7 @@ __global__ void __launch_bounds__(kTmThreads, 1) k_tree_mma(const __grid_constan
       tc::mbar_init(&bar_afull[i], 1);
       tc::mbar_init(&bar_aempty[i], 1);
     }
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < kTmSlots; ++i) {
       tc::mbar_init(&bar_accfull[i], 1);
       tc::mbar_init(&bar_accempty[i], kTmEpiWarps * 32);
     }
@@ -151,8 +153,8 @@ __global__ void __launch_bounds__(kTmThreads, 1) k_tree_mma(const __grid_constan
     for (int i = 0; i < n_ap && ok; ++i) {
       const int b = i % kTmABufs;
       const uint32_t use = (uint32_t)(i / kTmABufs);
-      const int slot = i & 1;
-      const uint32_t su = (uint32_t)(i >> 1);
+      const int slot = i % kTmSlots;
+      const uint32_t su = (uint32_t)(i / kTmSlots);
       if (!__all_sync(0xffffffffu, tc::mbar_wait(&bar_afull[b], use & 1, abortp, t.timeout))) {
         ok = false;
         break;
@@ -202,7 +204,7 @@ __global__ void __launch_bounds__(kTmThreads, 1) k_tree_mma(const __grid_constan
 #pragma unroll
       for (int j = 0; j < 16; ++j) z[j] = 0.f;
       for (int a = 0; a + 2 <= t.nlev; ++a) {
-        const uint32_t ab = lane_base + (uint32_t)(2 * kTmCols + a * kTmCols);
+        const uint32_t ab = lane_base + (uint32_t)((kTmSlots + a) * kTmCols);
         tm_st16(ab + c_re, z);
         tm_st16(ab + c_im, z);
       }
@@ -210,86 +212,90 @@ __global__ void __launch_bounds__(kTmThreads, 1) k_tree_mma(const __grid_constan
     }
     bool ok = true;
     for (int i = 0; i < n_ap; ++i) {
-      const int k = kb + i, slot = i & 1, buf = i & 1;
-      const uint32_t su = (uint32_t)(i >> 1);
+      const int k = kb + i, slot = i % kTmSlots, pslot = (i + kTmSlots - 1) % kTmSlots, buf = i & 1;
+      const uint32_t su = (uint32_t)(i / kTmSlots);
       if (ok && !tc::mbar_wait(&bar_accfull[slot], su & 1, abortp, t.timeout)) ok = false;
-      if (!__all_sync(0xffffffffu, ok)) ok = false;  // tcgen05.ld below is warp-collective
-      if (named_sync_or_epi(!ok)) ok = false;
-      if (!ok) break;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      float cre[16], cim[16], pre[16], pim[16];
-      const uint32_t cur = lane_base + (uint32_t)(slot * kTmCols), prv = lane_base + (uint32_t)((slot ^ 1) * kTmCols);
-      tm_ld16(cur + c_re, cre);
-      tm_ld16(cur + c_im, cim);
-      if (i > 0) {
-        tm_ld16(prv + c_re, pre);
-        tm_ld16(prv + c_im, pim);
-      } else {
-#pragma unroll
-        for (int j = 0; j < 16; ++j) pre[j] = pim[j] = 0.f;
-      }
-      tm_wait_ld();
-      if (i > 0) {  // G_1(k - 1) is read: its slot may take AP k + 1
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        tc::mbar_arrive(&bar_accempty[slot ^ 1]);
-      }
+      ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
       const int ctz = __ffs(k + 1) - 1;
       const int E = t.nlev == 0 ? 0 : min(t.nlev, ctz + 1);
-      float are[16], aim[16];
-#pragma unroll
-      for (int e = 0; e <= kTmMaxLev; ++e) {
-        if (e > E) break;
-        if (e == 0) {
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            are[j] = cre[j];
-            aim[j] = cim[j];
-          }
-        } else if (e == 1) {
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            are[j] = pre[j] + cre[j];
-            aim[j] = pim[j] + cim[j];
-          }
+      if (ok) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        float cre[16], cim[16], pre[16], pim[16];
+        const uint32_t cur = lane_base + (uint32_t)(slot * kTmCols), prv = lane_base + (uint32_t)(pslot * kTmCols);
+        tm_ld16(cur + c_re, cre);
+        tm_ld16(cur + c_im, cim);
+        if (i > 0) {
+          tm_ld16(prv + c_re, pre);
+          tm_ld16(prv + c_im, pim);
         } else {
-          // anchor of level e - 1: the previous window-2^(e-1) matrix, first half of this one
-          const uint32_t ab = lane_base + (uint32_t)(2 * kTmCols + (e - 2) * kTmCols);
-          float ore[16], oim[16];
-          tm_ld16(ab + c_re, ore);
-          tm_ld16(ab + c_im, oim);
-          tm_wait_ld();
-          tm_st16(ab + c_re, are);
-          tm_st16(ab + c_im, aim);
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            are[j] += ore[j];
-            aim[j] += oim[j];
-          }
-          tm_wait_st();
+          for (int j = 0; j < 16; ++j) pre[j] = pim[j] = 0.f;
         }
-        const int w = t.emit_w[e];
-        const int k0 = k - (1 << e) + 1;
-        if (w >= 0 && k0 >= kb && k0 < kb + t.TT) {  // uniform across the CTA
-          // packed key: |G|^2 with its 6 low mantissa bits replaced by 31 - j (lower q wins a tie)
-          unsigned kk[16];
+        tm_wait_ld();
+        if (i > 0) {  // G_1(k - 1) is read: its slot may take AP k + 2
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          tc::mbar_arrive(&bar_accempty[pslot]);
+        }
+        float are[16], aim[16];
 #pragma unroll
-          for (int j = 0; j < 16; ++j)
-            kk[j] = (__float_as_uint(fmaf(are[j], are[j], aim[j] * aim[j])) & ~63u) | (unsigned)(31 - j);
+        for (int e = 0; e <= kTmMaxLev; ++e) {
+          if (e > E) break;
+          if (e == 0) {
 #pragma unroll
-          for (int wdt = 8; wdt >= 1; wdt >>= 1) {
+            for (int j = 0; j < 16; ++j) {
+              are[j] = cre[j];
+              aim[j] = cim[j];
+            }
+          } else if (e == 1) {
 #pragma unroll
-            for (int j = 0; j < wdt; ++j) kk[j] = max(kk[j], kk[j + wdt]);
+            for (int j = 0; j < 16; ++j) {
+              are[j] = pre[j] + cre[j];
+              aim[j] = pim[j] + cim[j];
+            }
+          } else {
+            // anchor of level e - 1: the previous window-2^(e-1) matrix, first half of this one
+            const uint32_t ab = lane_base + (uint32_t)((kTmSlots + e - 2) * kTmCols);
+            float ore[16], oim[16];
+            tm_ld16(ab + c_re, ore);
+            tm_ld16(ab + c_im, oim);
+            tm_wait_ld();
+            tm_st16(ab + c_re, are);
+            tm_st16(ab + c_im, aim);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              are[j] += ore[j];
+              aim[j] += oim[j];
+            }
+            tm_wait_st();
           }
-          const unsigned wmax = __reduce_max_sync(0xffffffffu, kk[0]);
-          const unsigned win = __ballot_sync(0xffffffffu, kk[0] == wmax);
-          if (lane == 0) {
-            const int L = __ffs(win) - 1;
-            const int j = 31 - (int)(wmax & 63u);
-            red[buf][e][warp] = make_uint2(wmax & ~63u, (unsigned)((quarter * 32 + L) * t.Lm + q0 + j));
+          const int w = t.emit_w[e];
+          const int k0 = k - (1 << e) + 1;
+          if (w >= 0 && k0 >= kb && k0 < kb + t.TT) {  // uniform across the CTA
+            // packed key: |G|^2 with its 6 low mantissa bits replaced by 31 - j (lower q wins a tie)
+            unsigned kk[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              kk[j] = (__float_as_uint(fmaf(are[j], are[j], aim[j] * aim[j])) & ~63u) | (unsigned)(31 - j);
+#pragma unroll
+            for (int wdt = 8; wdt >= 1; wdt >>= 1) {
+#pragma unroll
+              for (int j = 0; j < wdt; ++j) kk[j] = max(kk[j], kk[j + wdt]);
+            }
+            const unsigned wmax = __reduce_max_sync(0xffffffffu, kk[0]);
+            const unsigned win = __ballot_sync(0xffffffffu, kk[0] == wmax);
+            if (lane == 0) {
+              const int L = __ffs(win) - 1;
+              const int j = 31 - (int)(wmax & 63u);
+              red[buf][e][warp] = make_uint2(wmax & ~63u, (unsigned)((quarter * 32 + L) * t.Lm + q0 + j));
+            }
           }
         }
       }
-      named_sync_epi();
+      // one barrier per AP, which also makes a give-up uniform across the epilogue warps
+      if (named_sync_or_epi(!ok)) {
+        ok = false;
+        break;
+      }
       // merge the block's maxima of the segments emitted at AP k into the series
       if (tid <= E) {
         const int e = tid, w = t.emit_w[e], k0 = k - (1 << e) + 1;
