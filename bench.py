@@ -44,6 +44,8 @@ FIT_DRAM_BYTES_PER_SEGMENT = None
 # covers, from an ncu capture of the vgos-profile workload (2.590 + 0.045 GB over
 # 4 x 20000 series-APs); set to None when k_tree_mbd changes
 TREE_MBD_DRAM_BYTES_PER_AP = (2.589522e9 + 0.045097e9) / (4 * 20000)
+# the same for k_tree_mma (the tensor-core MBD pass): 2.791 + 0.006 GB over 4 x 20000
+TREE_MMA_DRAM_BYTES_PER_AP = (2.791194e9 + 0.006259e9) / (4 * 20000)
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 
 
@@ -371,17 +373,26 @@ def main():
     tree = stages["tree_chunks"] > 0
     hbm_frac = (8.0 * cells / (ms / 1e3)) / (peaks["hbm_gbs"] * 1e9)
     if tree:
-        # dominant kernel: the MBD pass of the window-tree fit (k_tree_mbd), timed per chunk
-        # with CUDA events on the library's chunk streams; it emits every segment
+        # dominant kernel: the MBD pass of the window-tree fit (k_tree_mbd, or k_tree_mma on the
+        # tensor cores), timed per chunk with CUDA events on the library's stream; it emits
+        # every segment
+        tc = stages["tree_tensor"] > 0
         kms = statistics.mean(mbd_ms)
         achieved = flops / (kms / 1e3) / 1e12
         n_ap = wl.n_bl * sum(max(0, wl.T - int(x)) for x in dk_max)
         n_l1 = n_ap if 1 in wl.windows else 0
-        executed = (n_ap * h.Ls * 5 * h.Lm * math.log2(h.Lm) + (n_seg - n_l1) * 2 * h.Ls * h.Lm
-                    + n_seg * 3 * h.Ls * h.Lm)
+        epilogue = (n_seg - n_l1) * 2 * h.Ls * h.Lm + n_seg * 3 * h.Ls * h.Lm
+        if tc:  # three BF16 GEMMs of Ls x 2N (padded to 64-wide K atoms) x 2 Lm per AP
+            gemm = n_ap * 3 * 2 * h.Ls * (64 * ((2 * wl.n_chan + 63) // 64)) * 2 * h.Lm
+            executed = epilogue
+        else:
+            gemm = 0
+            executed = n_ap * h.Ls * 5 * h.Lm * math.log2(h.Lm) + epilogue
         launches_ = max(1, int(stages["tree_chunks"]))
-        traffic = None if TREE_MBD_DRAM_BYTES_PER_AP is None else TREE_MBD_DRAM_BYTES_PER_AP * n_ap / launches_
-        roof = {"bound": "alu", "kernel": "k_tree_mbd", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+        per_ap = TREE_MMA_DRAM_BYTES_PER_AP if tc else TREE_MBD_DRAM_BYTES_PER_AP
+        traffic = None if per_ap is None else per_ap * n_ap / launches_
+        roof = {"bound": "alu", "kernel": "k_tree_mma" if tc else "k_tree_mbd", "achieved": achieved,
+                "peak": FP32_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
                 "traffic_note": "bytes per launch, scaled by series-APs from the vgos-profile ncu capture",
                 "peak_note": "FP32 CUDA-core peak 152 SM x 128 lanes x 2 flop x 2070 MHz (derived, not measured)",
@@ -390,9 +401,17 @@ def main():
                 "kernel_ms": kms, "launches": int(stages["tree_chunks"]), "fit_ms": fit_mean,
                 "executed": {"achieved": executed / (kms / 1e3) / 1e12,
                              "frac": executed / (kms / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
-                             "work": f"{n_ap} AP transforms x Ls 5 Lm log2 Lm + 2 Ls Lm per summed window "
-                                     "+ 3 Ls Lm per emitted segment (flop the kernel actually performs)"},
+                             "work": ("2 Ls Lm per summed window + 3 Ls Lm per emitted segment (CUDA cores)"
+                                      if tc else
+                                      f"{n_ap} AP transforms x Ls 5 Lm log2 Lm + 2 Ls Lm per summed window "
+                                      "+ 3 Ls Lm per emitted segment (flop the kernel actually performs)")},
                 "hbm_frac_8B_per_cell": hbm_frac, "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_kind": peaks_kind}
+        if tc:
+            roof["executed_tensor"] = {
+                "achieved": gemm / (kms / 1e3) / 1e12, "peak": peaks["bf16_tflops_sustained"],
+                "frac": gemm / (kms / 1e3) / 1e12 / peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                "peak_kind": peaks_kind + " sustained bf16",
+                "work": f"{n_ap} APs x 3 BF16 GEMMs (split operands) of the MBD transform"}
     else:
         achieved = flops / (fit_mean / 1e3) / 1e12
         kname = ("k_fit_mma" if args.kernel in (3, 5) else
@@ -408,6 +427,9 @@ def main():
     line = {"metric": metric, "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded, synth.py)", "config": cfg,
+            "dtype_note": ("f32 arithmetic; the window-tree MBD transform runs on the tensor cores as "
+                           "three BF16 products of split operands with f32 accumulation "
+                           "(f32-equivalent, about 1e-5 relative)") if stages["tree_tensor"] > 0 else "f32 arithmetic",
             "e2e": {"value": world * cells / (e2e / 1e3), "unit": "cells/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e},
             "gpu_launches": launches, "roofline": roof, "clocks": clocks,

@@ -86,8 +86,20 @@ typedef struct frbx_setup {
  *                MBD(q) = (s(q) * 1000) / (Lm * df_grid), s(i) = i if i < L/2 else i - L.
  *  combos        [n_combo] baseline bit masks for the power-summation scheme
  *                (Sec. 2.4.2); bit b = baseline b.  May be NULL when n_combo = 0.
- *  kernel        0 = choose automatically, 1 = direct-DFT fit kernel,
- *                2 = FFT fit kernel (needs Ls and Lm multiples of 32).
+ *  kernel        how Eq. 5 is evaluated on the Sec. 5.1 grid (all give the same results
+ *                within FP32 rounding unless stated):
+ *                0 = choose automatically: 6 where it applies, else 4, else 2, else 1;
+ *                1 = direct DFT per segment;
+ *                2 = per-segment four-step FFT (Ls and Lm multiples of 32);
+ *                3 = per-segment BF16 tensor-core DFT-GEMM (about 4e-3 relative error;
+ *                    Ls 64 or 128, whole grid);
+ *                4 = window tree: power-of-two windows built from one-AP matrices by the
+ *                    additivity of Sec. 5.1, FP32 on the CUDA cores (windows <= 64 APs);
+ *                5 = as 3 with FP8 E4M3 operands (about 6e-2 relative error);
+ *                6 = window tree with the MBD transform as a three-term split-BF16
+ *                    tensor-core GEMM, FP32 accumulation (about 1e-5 relative; Ls 128,
+ *                    n_chan <= 64, whole grid).
+ *                frbx_fit_segments treats 4 and 6 as 0 (a list has no window structure).
  */
 typedef struct frbx_params {
   float threshold;
@@ -295,13 +307,14 @@ int frbx_extract_events(const frbx_event *events, int64_t n_events, int32_t n_se
  *  [2] baselines: Eq. 6 + threshold  [3] combinations: sum + Eq. 6 + threshold
  *  [4] host extraction (Sec. 2.4.1 b-d, Sec. 5.3 merge, cross-matching, Sec. 2.4.2)
  *  [5] window-tree fit: device time of its SBD-pass kernels, summed over its chunks
- *  [6] window-tree fit: device time of its MBD-pass kernels (k_tree_mbd), summed
+ *  [6] window-tree fit: device time of its MBD-pass kernels (k_tree_mbd or k_tree_mma), summed
  *  [7] window-tree fit: number of chunks (= launches of each of the two kernels)
+ *  [8] window-tree fit: 1 if its MBD pass ran on the tensor cores (k_tree_mma), else 0
  *  ms_out  [n] out, milliseconds (stages that did not run report 0).
  * Stages [5] and [6] are bracketed by events on the library's own streams (SBD passes on
  * one, MBD passes on the other); the SBD pass of a chunk overlaps the MBD pass of the
  * previous one, so [5] + [6] can exceed [1].
- * Returns the number of values written (min(n, 8)) or FRBX_EINVAL.
+ * Returns the number of values written (min(n, 9)) or FRBX_EINVAL.
  */
 int frbx_last_stage_times(const frbx_handle *h, double *ms_out, int32_t n);
 
@@ -417,8 +430,8 @@ int frbx_batch_info(const frbx_batch *b, frbx_batch_stats *stats);
 
 /*
  *  scans     [n_scans] (1..4096; at most 16 distinct setups).
- *  dm, n_dm, windows, n_win, params  as in frbx_search, shared by all scans (kernel 0, 1 or 2;
- *            combination masks must name baselines each scan has).
+ *  dm, n_dm, windows, n_win, params  as in frbx_search, shared by all scans (kernel 0, 1, 2,
+ *            4 or 6; combination masks must name baselines each scan has).
  *  results   [n_scans] outputs, one frbx_results per scan (series outputs included).
  * Errors: FRBX_EINVAL, FRBX_ENOMEM, FRBX_ECUDA, FRBX_ETRUNC, FRBX_EUNSUPPORTED.
  */

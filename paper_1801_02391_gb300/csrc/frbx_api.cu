@@ -738,6 +738,7 @@ int enqueue_tree(frbx_handle *h, const FitArgs &a, const TreeRun &r, const int2 
         h->tree_kev.push_back(ev);
       }
       h->tree_chunks = n_chunks;
+      h->tree_tensor = t.mma ? 1 : 0;
     }
     int ci = 0;
     for (size_t c0 = 0; c0 < r.ser.size(); c0 += r.chunk, ++ci) {
@@ -880,6 +881,7 @@ int finish_search(frbx_handle *h, const frbx_seg *series, int n_bl, int T, const
       h->stage_ms[6] += ms;
     }
     h->stage_ms[7] = h->tree_chunks;
+    h->stage_ms[8] = h->tree_chunks > 0 ? h->tree_tensor : 0;
   }
   const auto host_t0 = std::chrono::steady_clock::now();
 
@@ -1170,7 +1172,7 @@ extern "C" int frbx_extract_events(const frbx_event *events, int64_t n_events, i
 
 extern "C" int frbx_last_stage_times(const frbx_handle *h, double *ms_out, int32_t n) {
   if (!h || !ms_out || n < 0) return FRBX_EINVAL;
-  const int k = std::min(n, 8);
+  const int k = std::min(n, 9);
   for (int i = 0; i < k; ++i) ms_out[i] = h->stage_ms[i];
   return k;
 }

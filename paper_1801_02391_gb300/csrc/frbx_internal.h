@@ -231,7 +231,7 @@ struct frbx_handle {
   std::string err;
   int64_t launches = 0;
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  double stage_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  double stage_ms[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   // constant device tables
   double *d_f = nullptr, *d_f0 = nullptr;
   float2 *d_wrot = nullptr, *d_tw_s = nullptr, *d_tw_m = nullptr;
@@ -243,6 +243,7 @@ struct frbx_handle {
   cudaEvent_t tree_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // start, SBD done x2, MBD done x2
   std::vector<cudaEvent_t> tree_kev;  // per window-tree chunk: SBD start / end, MBD start / end
   int tree_chunks = 0;               // chunks of the last window-tree fit (0: another kernel ran)
+  int tree_tensor = 0;               // 1: its MBD pass ran on the tensor cores (k_tree_mma)
   void *d_bimg = nullptr;  // BF16 DFT matrix image for the tensor-core fit (if supported)
   void *d_bimg8 = nullptr;  // the same matrix in E4M3
   void *d_wtree = nullptr;  // window-tree tensor-core fit: split-BF16 DFT blocks of 32 q

@@ -313,12 +313,12 @@ class Handle:
         return int(load().frbx_last_launch_count(self.h))
 
     STAGES = ("shift_table", "fit", "normalise_baselines", "normalise_combos", "host_extract",
-              "tree_sbd_kernels", "tree_mbd_kernels", "tree_chunks")
+              "tree_sbd_kernels", "tree_mbd_kernels", "tree_chunks", "tree_tensor")
 
     def stage_times(self) -> dict:
         """Milliseconds per stage of the last search (CUDA events on its stream)."""
-        out = np.zeros(8, np.float64)
-        n = load().frbx_last_stage_times(self.h, _ptr(out, c_f64), 8)
+        out = np.zeros(9, np.float64)
+        n = load().frbx_last_stage_times(self.h, _ptr(out, c_f64), 9)
         if n < 0:
             raise FrbxError(n, "frbx_last_stage_times")
         return dict(zip(self.STAGES, out.tolist()))
