@@ -351,11 +351,12 @@ int frbx_create(const frbx_setup *s, frbx_handle **out) {
     h->b_bytes8 = KA8 * rows * 128;
   }
   // window-tree tensor-core fit: per block of 32 MBD columns q, the DFT rows (Re G of the 32
-  // q, then Im G) split as W = W_hi + W_lo in BF16, each in its 128-byte swizzled image
+  // q, then Im G) split as W = W_hi + W_lo in BF16, in 128-byte swizzled images; per 64-wide
+  // K atom the 64 hi rows are followed by the 64 lo rows, so [W_hi; W_lo] is one 128-row operand
   std::vector<uint16_t> wtree;
   if (frbx::tree_mma_supported(h->Ls, h->Lm, N, J)) {
     const int KA = (2 * N + 63) / 64, rows = 64, n_qb = h->Lm / 32, atom = rows * 128;
-    const int wb = 2 * KA * atom;  // bytes per block: hi atoms, then lo atoms
+    const int wb = 2 * KA * atom;  // bytes per block: per K atom, hi rows then lo rows
     wtree.assign((size_t)n_qb * wb / 2, 0);
     auto bf16 = [](double v) {
       const float f = (float)v;
@@ -371,7 +372,7 @@ int frbx_create(const frbx_setup *s, frbx_handle **out) {
       return (double)f;
     };
     auto put = [&](int qb, int lo, int R, int k, uint16_t v) {
-      const size_t off = (size_t)qb * wb + (size_t)lo * KA * atom + (size_t)(k / 64) * atom + (size_t)(R / 8) * 1024 +
+      const size_t off = (size_t)qb * wb + (size_t)(k / 64) * 2 * atom + (size_t)lo * atom + (size_t)(R / 8) * 1024 +
                          (size_t)(R % 8) * 128 + (size_t)((((k % 64) / 8) ^ (R % 8)) * 16) + (size_t)(k % 8) * 2;
       wtree[off / 2] = v;
     };

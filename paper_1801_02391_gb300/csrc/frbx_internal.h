@@ -156,7 +156,7 @@ struct TreeArgs {
   size_t yt_series;        // bytes per series in Yt
   int KA;                  // 64-wide K atoms per tile row (K = 2N)
   int tile_bytes;          // one AP: hi tile then lo tile, 2 KA 16 KB
-  const unsigned char *wimg;  // [Lm/32][hi | lo][KA][64 rows x 128 B]
+  const unsigned char *wimg;  // [Lm/32][KA][hi | lo][64 rows x 128 B]
   int w_bytes;             // per block of 32 q: 2 KA 8 KB
   int n_qb;                // Lm / 32
   int log2Lm;
