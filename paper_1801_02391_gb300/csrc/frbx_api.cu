@@ -1082,7 +1082,8 @@ extern "C" int frbx_search(frbx_handle *h, const void *vis, int32_t vis_on_devic
   int nlev = 0;
   const bool tree_ok = frbx::tree_supported(h->Ls, h->Lm, h->N, h->J, h->tree_s16, windows, n_win, &nlev);
   const bool full_grid = a.m_lo == 0 && a.m_len == h->Ls && a.q_lo == 0 && a.q_len == h->Lm;
-  const bool tree_tc = tree_ok && full_grid && h->d_wtree && frbx::tree_mma_supported(h->Ls, h->Lm, h->N, h->J);
+  const bool tree_tc = tree_ok && full_grid && h->d_wtree && frbx::tree_mma_supported(h->Ls, h->Lm, h->N, h->J) &&
+                       frbx::tree_mma_fits(h->N, nlev);
   if ((p.kernel == 4 && !tree_ok) || (p.kernel == 6 && !tree_tc))
     return fail(h, FRBX_EUNSUPPORTED,
                 "window-tree fit needs power-of-two windows <= 64 and Ls, Lm multiples of 32 (tensor cores: Ls 128, "
@@ -1453,7 +1454,8 @@ extern "C" int frbx_search_batch(frbx_batch *b, const frbx_scan *scans, int32_t 
     int nlev = 0;
     const bool ok = frbx::tree_supported(h->Ls, h->Lm, h->N, h->J, h->tree_s16, windows, n_win, &nlev);
     const FitArgs &ag = fa[g];
-    const bool tc_ok = ok && h->d_wtree && frbx::tree_mma_supported(h->Ls, h->Lm, h->N, h->J) && ag.m_lo == 0 &&
+    const bool tc_ok = ok && h->d_wtree && frbx::tree_mma_supported(h->Ls, h->Lm, h->N, h->J) &&
+                       frbx::tree_mma_fits(h->N, nlev) && ag.m_lo == 0 &&
                        ag.m_len == h->Ls && ag.q_lo == 0 && ag.q_len == h->Lm;
     if ((p.kernel == 4 && !ok) || (p.kernel == 6 && !tc_ok))
       return bfail(b, FRBX_EUNSUPPORTED, "setup " + std::to_string(g) + ": window-tree fit does not apply");

@@ -162,8 +162,11 @@ struct TreeArgs {
   int log2Lm;
   int *err;                // set to FRBX_ETIMEOUT when a bounded wait of k_tree_mma gives up
   long long timeout;       // clock cycles per wait
+  int n_abuf;              // A-tile ring depth of k_tree_mma (set by its launcher)
+  int n_sanc;              // window-tree anchor levels of k_tree_mma in shared memory (set by its launcher)
 };
 bool tree_mma_supported(int Ls, int Lm, int N, int J);
+bool tree_mma_fits(int N, int nlev);  // shared memory holds W, the A ring and the deep anchors
 cudaError_t launch_tree_mma(const TreeArgs &t, cudaStream_t st, int64_t *launches);
 bool tree_supported(int Ls, int Lm, int N, int J, int s16, const int *windows, int n_win, int *nlev);
 size_t tree_anchor_floats(int nlev);  // float2 per MBD CTA in TreeArgs::anc_g

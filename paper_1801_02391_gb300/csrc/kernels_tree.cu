@@ -313,9 +313,9 @@ __global__ void __launch_bounds__(kTreeThreads, 3) k_tree_mbd(const __grid_const
           if (r2.x > best.x || (r2.x == best.x && r2.y < best.y)) best = r2;
         }
         if (best.x != 0u) {
-          const int l = 1 << e, step = l > 1 ? l / 2 : 1;
+          // windows of 2^e APs start every 2^(e-1) APs (every AP for e = 0); k0 >= 0
           const unsigned long long kv = ((unsigned long long)best.x << 32) | (unsigned long long)(~best.y);
-          atomicMax(keys + t.win_off[w] + k0 / step, kv);
+          atomicMax(keys + t.win_off[w] + (k0 >> (e > 0 ? e - 1 : 0)), kv);
         }
       }
     }
