@@ -41,11 +41,11 @@ FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12  #
 # current kernel).
 FIT_DRAM_BYTES_PER_SEGMENT = None
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_tree_mbd launch per (series, AP) it
-# covers, from an ncu capture of the vgos-profile workload (2.590 + 0.045 GB over
-# 4 x 20000 series-APs); set to None when k_tree_mbd changes
-TREE_MBD_DRAM_BYTES_PER_AP = (2.589522e9 + 0.045097e9) / (4 * 20000)
-# the same for k_tree_mma (the tensor-core MBD pass): 2.791 + 0.006 GB over 4 x 20000
-TREE_MMA_DRAM_BYTES_PER_AP = (2.791194e9 + 0.006259e9) / (4 * 20000)
+# covers, from an ncu capture of the vgos-profile workload; None: k_tree_mbd has changed since
+# its last capture
+TREE_MBD_DRAM_BYTES_PER_AP = None
+# the same for k_tree_mma (the tensor-core MBD pass): 2.827 + 0.006 GB over 4 x 20000
+TREE_MMA_DRAM_BYTES_PER_AP = (2.826652e9 + 0.006355e9) / (4 * 20000)
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 
 
