@@ -142,3 +142,17 @@ def test_tree_rejects_other_windows(frbx):
     # the automatic choice falls back to the per-segment fit for such windows
     out = h.search(to_dev(synth.generate(wl)), wl.dms, [3, 6], want_series=True)
     assert (out["series"]["amp"] >= 0).any()
+
+
+@pytest.mark.parametrize("windows", [[1, 2, 4, 8, 16, 32, 64], [2, 8, 32]])
+def test_tree_tensor_cores_two_k_atoms(frbx, windows):
+    """64 contiguous channels x 64 points: K = 2N = 128, two 64-wide K atoms per MMA row and
+    64 KB A tiles.  Windows up to 32 APs keep every anchor in tensor memory and a three-deep
+    A ring; windows of 64 APs put the deepest anchor level in shared memory, which leaves
+    room for a two-deep ring only."""
+    wl = synth.make_tiny(n_chan=64, n_point=64, T=420, n_bl=1, dms=(0.0, 8.0), windows=windows,
+                         f0=800.0 + 16.0 * np.arange(64))
+    wl.pulses = [synth.Pulse(dm=8.0, t0_bin=150, width=4, snr=25.0)]
+    h, _ = _run(frbx, wl, windows, combos=(1,), kernel=6)
+    assert (h.Ls, h.Lm) == (128, 128)
+    assert h.stage_times()["tree_tensor"] == 1
