@@ -86,11 +86,15 @@ __global__ void __launch_bounds__(kTreeThreads, 3)
   float4 *Yout = kSplit ? reinterpret_cast<float4 *>(const_cast<unsigned char *>(t.Yt) + (size_t)s * t.yt_series)
                         : reinterpret_cast<float4 *>(t.Y + (size_t)s * t.y_series);
   const int row4 = stage / 16;  // float4 per AP
+  // this thread's points p = tid + blockDim i: channel n and point j stepped without a division
+  const int dn = (int)blockDim.x / a.J, dj = (int)blockDim.x - dn * a.J;
+  const int n0 = (int)threadIdx.x / a.J, j0 = (int)threadIdx.x - n0 * a.J;
   __syncthreads();
   for (int k = k_lo; k < k_hi; ++k) {
     // Eq. 3 with l = 1: the dedispersed spectrum of AP k, weighted and rotated; kSbdBatch
     // independent cube loads in flight per thread (the shift-table row stays in L1)
     const size_t row0 = (size_t)sd.x * a.T + k;
+    int n = n0, j = j0;
     for (int p0 = threadIdx.x; p0 < a.C; p0 += blockDim.x * kSbdBatch) {
       float2 v[kSbdBatch];
 #pragma unroll
@@ -101,9 +105,12 @@ __global__ void __launch_bounds__(kTreeThreads, 3)
 #pragma unroll
       for (int q = 0; q < kSbdBatch; ++q) {
         const int p = p0 + q * (int)blockDim.x;
-        if (p < a.C) {
-          const int n = p / a.J, j = p - n * a.J;
-          X[n * xs + j] = cmul(v[q], __ldg(a.wrot + p));
+        if (p < a.C) X[n * xs + j] = cmul(v[q], __ldg(a.wrot + p));
+        n += dn;
+        j += dj;
+        if (j >= a.J) {
+          j -= a.J;
+          ++n;
         }
       }
     }
@@ -375,7 +382,11 @@ bool tree_supported(int Ls, int Lm, int N, int J, int s16, const int *windows, i
     lmax = std::max(lmax, l);
   }
   *nlev = __builtin_ctz((unsigned)lmax);
-  return tree_smem_bytes(NS, PM, RB, *nlev) <= max_smem_optin();
+  // the SBD pass holds one AP of output (Ls N complex, the same bytes as the split tiles of the
+  // tensor-core form), the gathered points and its twiddles
+  const int JP = (J + 31) / 32 * 32;
+  const size_t sbd = sizeof(float2) * ((size_t)Ls * N + (size_t)N * (JP + 1) + (size_t)(Ls / 32) * (JP + 1));
+  return tree_smem_bytes(NS, PM, RB, *nlev) <= max_smem_optin() && sbd <= max_smem_optin();
 }
 
 size_t tree_anchor_floats(int nlev) { return (size_t)tree_global_anchors(nlev) * 16 * kTreeThreads; }

@@ -407,11 +407,12 @@ __global__ void __launch_bounds__((kEpi + 2) * 32, 1) k_tree_mma(const __grid_co
 #pragma unroll
             for (int j = 0; j < wdt; ++j) kk[j] = max(kk[j], kk[j + wdt]);
           }
+          // the lane holding the warp maximum merges it; tied lanes share j, and the atomicMax
+          // keeps the lowest of their indices, the lowest lane
           const unsigned wmax = __reduce_max_sync(0xffffffffu, kk[0]);
-          const unsigned win = __ballot_sync(0xffffffffu, kk[0] == wmax);
-          if (lane == 0) {
-            const unsigned L = (unsigned)(__ffs(win) - 1), j = 31u - (wmax & 63u);
-            const unsigned idx = idx0 + L * (unsigned)t.Lm + j;
+          if (kk[0] == wmax) {
+            const unsigned j = 31u - (wmax & 63u);
+            const unsigned idx = idx0 + (unsigned)lane * (unsigned)t.Lm + j;
             // slot of the segment: windows of 2^e APs start every 2^(e-1) APs (every AP for e = 0)
             atomicMax(keys + woff[e] + (k0 >> (e > 0 ? e - 1 : 0)),
                       ((unsigned long long)(wmax & ~63u) << 32) | (unsigned long long)(~idx));

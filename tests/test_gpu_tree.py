@@ -156,3 +156,21 @@ def test_tree_tensor_cores_two_k_atoms(frbx, windows):
     h, _ = _run(frbx, wl, windows, combos=(1,), kernel=6)
     assert (h.Ls, h.Lm) == (128, 128)
     assert h.stage_times()["tree_tensor"] == 1
+
+
+def test_tree_rejects_shapes_beyond_shared_memory(frbx):
+    """64 channels x 256 points: Ls = 512 SBD rows, so one AP of SBD output (256 KB) exceeds
+    shared memory.  The window trees refuse the shape up front (no failed launch), and so does
+    the automatic choice, since no per-segment fit holds it either."""
+    wl = synth.make_tiny(n_chan=64, n_point=256, T=40, n_bl=1, dms=(0.0,), windows=(1, 2),
+                         f0=800.0 + 16.0 * np.arange(64), pulse=False)
+    h = frbx.Handle.from_workload(wl)
+    assert h.Ls == 512
+    vis = to_dev(synth.generate(wl))
+    for k in (4, 6):
+        with pytest.raises(frbx.FrbxError) as e:
+            h.search(vis, wl.dms, [1, 2], kernel=k)
+        assert e.value.code == frbx.FRBX_EUNSUPPORTED
+    with pytest.raises(frbx.FrbxError) as e:
+        h.search(vis, wl.dms, [1, 2])
+    assert e.value.code == frbx.FRBX_EUNSUPPORTED
