@@ -130,13 +130,25 @@ __global__ void __launch_bounds__(kTreeThreads, 3)
       fft32_dif(A);
       if (kSplit) {
         const int half = t.tile_bytes / 2;
+        // Ls = 128 rows (PS = 4): row = m1 + 4 b with b = bitrev5(i), so row / 8 = b / 2 and
+        // row % 8 = m1 + 4 (b % 2); the swizzled offsets of columns n and N + n for even and odd
+        // b are fixed per thread, and each element adds its 1 KB row group
+        uint32_t o_re[2] = {0u, 0u}, o_im[2] = {0u, 0u};
+        if (PS == 4) {
+#pragma unroll
+          for (int odd = 0; odd < 2; ++odd) {
+            o_re[odd] = tc::a_offset(m1 + 4 * odd, n);
+            o_im[odd] = tc::a_offset(m1 + 4 * odd, N + n);
+          }
+        }
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
-          const int row = m1 + PS * bitrev5(i);
+          const int b = bitrev5(i), row = m1 + PS * b;
           const __nv_bfloat16 rh = __float2bfloat16_rn(A[i].x), ih = __float2bfloat16_rn(A[i].y);
           const __nv_bfloat16 rl = __float2bfloat16_rn(A[i].x - __bfloat162float(rh));
           const __nv_bfloat16 il = __float2bfloat16_rn(A[i].y - __bfloat162float(ih));
-          const uint32_t orr = tc::a_offset(row, n), oi = tc::a_offset(row, N + n);
+          const uint32_t orr = PS == 4 ? o_re[b & 1] + (uint32_t)(b >> 1) * 1024u : tc::a_offset(row, n);
+          const uint32_t oi = PS == 4 ? o_im[b & 1] + (uint32_t)(b >> 1) * 1024u : tc::a_offset(row, N + n);
           *reinterpret_cast<__nv_bfloat16 *>(Yb + orr) = rh;
           *reinterpret_cast<__nv_bfloat16 *>(Yb + oi) = ih;
           *reinterpret_cast<__nv_bfloat16 *>(Yb + half + orr) = rl;
