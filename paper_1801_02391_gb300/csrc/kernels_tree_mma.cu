@@ -13,17 +13,19 @@
 // series and walks a time tile AP by AP (10 warps):
 //   warp 9 (one lane) copies each AP's split A tiles (written by k_tree_sbd in their
 //          shared-memory image) into a ring with cp.async.bulk;
-//   warp 8 allocates tensor memory and one of its lanes issues an AP's MMAs into one of three
-//          accumulator slots, so it runs up to two APs ahead.  A tcgen05.mma of M = 128 and
-//          K = 16 costs about the same for N = 64 and N = 128, so the two products of A_hi are
-//          one N = 128 MMA against the stacked [W_hi; W_lo], D = [A_hi W_hi | A_hi W_lo +
-//          A_lo W_hi], and the epilogue adds the halves: 2 K/16 MMAs per AP instead of 3 K/16;
+//   warp 8 allocates tensor memory and one of its lanes issues an AP's MMAs into one of two
+//          accumulator slots of 128 columns, so it runs one AP ahead.  A tcgen05.mma of
+//          M = 128 and K = 16 costs about the same for N = 64 and N = 128, so the two products
+//          of A_hi are one N = 128 MMA against the stacked [W_hi; W_lo], D = [A_hi W_hi |
+//          A_hi W_lo + A_lo W_hi], and the epilogue adds the halves: 2 K/16 MMAs per AP
+//          instead of 3 K/16;
 //   warps 0-7 (row quarter w % 4, q half w / 4) read G_1(k) into registers (freeing its slot
 //          at once), keep it there as G_1(k - 1) for the next AP, walk their 16 cells through
-//          the window tree with packed FP32x2 arithmetic (the anchors of windows 2 and 4 in
-//          tensor memory, deeper ones, read every 8 APs or less often, in shared memory), and
-//          merge every emitted segment's warp maximum into the series by a 64-bit atomicMax,
-//          as k_tree_mbd does per block: the warps never wait for one another.
+//          the window tree with packed FP32x2 arithmetic (the anchors of levels 2 to 5, the
+//          first halves of windows 4 to 32, in tensor memory after the slots; a level-6
+//          anchor, used every 32 APs, in shared memory), and merge every emitted segment's
+//          warp maximum into the series by a 64-bit atomicMax, as k_tree_mbd does per block:
+//          the warps never wait for one another.
 // Every wait is bounded: on timeout the kernel records FRBX_ETIMEOUT, drains and frees its
 // tensor memory.
 #include <cuda_bf16.h>
