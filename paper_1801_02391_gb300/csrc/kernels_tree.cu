@@ -60,7 +60,7 @@ __host__ __device__ inline size_t tree_smem_bytes(int NS, int PM, int RB, int nl
 // its shared-memory image: A_hi = bf16(Y) then A_lo = bf16(Y - A_hi), 128 rows x K = 2N
 // (Re Y of the channels, then Im Y), 128-byte swizzled K atoms.
 template <bool kSplit>
-__global__ void __launch_bounds__(kTreeThreads, 3)
+__global__ void __launch_bounds__(kTreeThreads, 4)
     k_tree_sbd(const __grid_constant__ FitArgs a, const __grid_constant__ TreeArgs t) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int N = a.N, Ls = a.Ls, PS = Ls >> 5, lps = __ffs(PS) - 1;
