@@ -33,10 +33,6 @@ sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
 
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
-SM_MAX_MHZ = 2070.0
-FP32_PEAK_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12  # 80.5
 # DRAM bytes per fitted segment of the per-segment fit kernel (None: no capture of the
 # current kernel).
 FIT_DRAM_BYTES_PER_SEGMENT = None
@@ -57,6 +53,22 @@ def measured_peaks():
         return {k: float(d[k]) for k in FALLBACK_PEAKS}, "measured"
     except (OSError, KeyError, ValueError):
         return dict(FALLBACK_PEAKS), "fallback"
+
+
+def measure_peaks(stream):
+    """This GPU's own peak rates (libfrbx_peaks): the FP32 FMA pipe (scalar and packed f32x2)
+    and the dense BF16 / E4M3 tcgen05 MMA, each as a burst (a few ms) and, for the MMAs, as a
+    sustained run of about 1.5 s; TFLOP/s with 2 flop per multiply-add."""
+    from paper_1801_02391_gb300 import peaks
+    out = {}
+    for k, it in (("fp32_fma", 20000), ("fp32_fma2", 20000)):
+        out[k] = peaks.probe(k, it, stream)[0]
+    for k, it in (("bf16_mma", 4000), ("fp8_mma", 4000)):
+        tf, ms = peaks.probe(k, it, stream)
+        out[k] = tf
+        out[k + "_sustained"] = peaks.probe(k, max(1, int(it * 1500.0 / max(ms, 1e-3))), stream)[0]
+    out["fp32"] = max(out["fp32_fma"], out["fp32_fma2"])
+    return out
 
 
 def parse():
@@ -328,6 +340,7 @@ def main():
     def step(vis):
         return h.search(vis, wl.dms, wl.windows, combos=combos, kernel=args.kernel, stream=stream)
 
+    line_peaks = measure_peaks(stream)
     for _ in range(args.warmup):
         out = step(vis_dev)
     barrier()
@@ -367,72 +380,77 @@ def main():
     e2e = max_over_ranks(statistics.mean(e2e_ms))
 
     peaks, peaks_kind = measured_peaks()
+    own = line_peaks  # this GPU's own probes, measured before the warm-up
     seg_flop = fft_flops_per_segment(wl.n_chan, h.Ls, h.Lm)
     flops = n_seg * seg_flop
     fit_mean = statistics.mean(fit_ms)
     tree = stages["tree_chunks"] > 0
+    tc = tree and stages["tree_tensor"] > 0
     hbm_frac = (8.0 * cells / (ms / 1e3)) / (peaks["hbm_gbs"] * 1e9)
+    bf16_peak = peaks["bf16_tflops_sustained"]
     if tree:
-        # dominant kernel: the MBD pass of the window-tree fit (k_tree_mbd, or k_tree_mma on the
-        # tensor cores), timed per chunk with CUDA events on the library's stream; it emits
-        # every segment
-        tc = stages["tree_tensor"] > 0
+        # dominant kernel: the MBD pass of the window-tree fit (k_tree_mma on the tensor cores,
+        # or k_tree_mbd on the CUDA cores), timed per chunk with CUDA events on the library's
+        # stream it runs on; it emits every segment
         kms = statistics.mean(mbd_ms)
         achieved = flops / (kms / 1e3) / 1e12
         n_ap = wl.n_bl * sum(max(0, wl.T - int(x)) for x in dk_max)
         n_l1 = n_ap if 1 in wl.windows else 0
         epilogue = (n_seg - n_l1) * 2 * h.Ls * h.Lm + n_seg * 3 * h.Ls * h.Lm
-        if tc:  # three BF16 GEMMs of Ls x 2N (padded to 64-wide K atoms) x 2 Lm per AP
-            gemm = n_ap * 3 * 2 * h.Ls * (64 * ((2 * wl.n_chan + 63) // 64)) * 2 * h.Lm
-            executed = epilogue
-        else:
-            gemm = 0
-            executed = n_ap * h.Ls * 5 * h.Lm * math.log2(h.Lm) + epilogue
         launches_ = max(1, int(stages["tree_chunks"]))
         per_ap = TREE_MMA_DRAM_BYTES_PER_AP if tc else TREE_MBD_DRAM_BYTES_PER_AP
         traffic = None if per_ap is None else per_ap * n_ap / launches_
-        roof = {"bound": "alu", "kernel": "k_tree_mma" if tc else "k_tree_mbd", "achieved": achieved,
-                "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
-                "traffic_note": "bytes per launch, scaled by series-APs from the vgos-profile ncu capture",
-                "peak_note": "FP32 CUDA-core peak 152 SM x 128 lanes x 2 flop x 2070 MHz (derived, not measured)",
-                "work": f"{n_seg} segments x {seg_flop:.0f} flop (2-D FFT count of the method per segment) "
-                        f"over {int(stages['tree_chunks'])} launches",
-                "kernel_ms": kms, "launches": int(stages["tree_chunks"]), "fit_ms": fit_mean,
-                "executed": {"achieved": executed / (kms / 1e3) / 1e12,
-                             "frac": executed / (kms / 1e3) / 1e12 / FP32_PEAK_TFLOPS,
-                             "work": ("2 Ls Lm per summed window + 3 Ls Lm per emitted segment (CUDA cores)"
-                                      if tc else
-                                      f"{n_ap} AP transforms x Ls 5 Lm log2 Lm + 2 Ls Lm per summed window "
-                                      "+ 3 Ls Lm per emitted segment (flop the kernel actually performs)")},
-                "hbm_frac_8B_per_cell": hbm_frac, "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_kind": peaks_kind}
-        if tc:
-            roof["executed_tensor"] = {
-                "achieved": gemm / (kms / 1e3) / 1e12, "peak": peaks["bf16_tflops_sustained"],
-                "frac": gemm / (kms / 1e3) / 1e12 / peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
-                "peak_kind": peaks_kind + " sustained bf16",
-                "work": f"{n_ap} APs x 3 BF16 GEMMs (split operands) of the MBD transform"}
+        work = (f"{n_seg} segments x {seg_flop:.0f} flop (the method's 2-D FFT count per segment, Sec. 5.1) "
+                f"over {launches_} launches")
+        if tc:  # three BF16 GEMMs of Ls x 2N (padded to 64-wide K atoms) x 2 Lm per AP
+            gemm = n_ap * 3 * 2 * h.Ls * (64 * ((2 * wl.n_chan + 63) // 64)) * 2 * h.Lm
+            roof = {"bound": "tensor", "kernel": "k_tree_mma", "achieved": achieved, "peak": bf16_peak,
+                    "unit": "TFLOP/s", "frac": achieved / bf16_peak, "traffic": traffic,
+                    "peak_kind": f"{peaks_kind} sustained bf16 (MEASURED_PEAKS.json, cuBLAS)",
+                    "work": work,
+                    "executed_tensor": {
+                        "achieved": gemm / (kms / 1e3) / 1e12, "peak": bf16_peak,
+                        "frac": gemm / (kms / 1e3) / 1e12 / bf16_peak, "unit": "TFLOP/s",
+                        "work": f"{n_ap} APs x 3 BF16 GEMMs (split operands) of the MBD transform, "
+                                "Ls x 2N x 2Lm each"},
+                    "executed_cuda_core": {
+                        "achieved": epilogue / (kms / 1e3) / 1e12, "peak": own["fp32"],
+                        "frac": epilogue / (kms / 1e3) / 1e12 / own["fp32"], "unit": "TFLOP/s",
+                        "peak_kind": "this GPU's FP32 FMA pipe, measured by libfrbx_peaks",
+                        "work": "2 Ls Lm per summed window + 3 Ls Lm per emitted segment"}}
+        else:
+            executed = n_ap * h.Ls * 5 * h.Lm * math.log2(h.Lm) + epilogue
+            roof = {"bound": "alu", "kernel": "k_tree_mbd", "achieved": achieved, "peak": own["fp32"],
+                    "unit": "TFLOP/s", "frac": achieved / own["fp32"], "traffic": traffic,
+                    "peak_kind": "this GPU's FP32 FMA pipe, measured by libfrbx_peaks", "work": work,
+                    "executed": {"achieved": executed / (kms / 1e3) / 1e12,
+                                 "frac": executed / (kms / 1e3) / 1e12 / own["fp32"],
+                                 "work": f"{n_ap} AP transforms x Ls 5 Lm log2 Lm + 2 Ls Lm per summed window "
+                                         "+ 3 Ls Lm per emitted segment"}}
+        roof.update({"traffic_note": "bytes per launch, scaled by series-APs from the vgos-profile ncu capture",
+                     "kernel_ms": kms, "launches": launches_, "fit_ms": fit_mean})
     else:
         achieved = flops / (fit_mean / 1e3) / 1e12
         kname = ("k_fit_mma" if args.kernel in (3, 5) else
                  "k_fit_fft" if (h.Ls % 32 == 0 and h.Lm % 32 == 0 and args.kernel != 1) else "k_fit_direct")
-        roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS,
+        roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": own["fp32"], "unit": "TFLOP/s",
+                "frac": achieved / own["fp32"],
                 "traffic": None if FIT_DRAM_BYTES_PER_SEGMENT is None else FIT_DRAM_BYTES_PER_SEGMENT * n_seg,
-                "peak_note": "FP32 CUDA-core peak 152 SM x 128 lanes x 2 flop x 2070 MHz (derived, not measured)",
-                "work": f"{n_seg} segments x {seg_flop:.0f} flop (2-D FFT count)",
-                "fit_ms": fit_mean, "hbm_frac_8B_per_cell": hbm_frac,
-                "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_kind": peaks_kind}
+                "peak_kind": "this GPU's FP32 FMA pipe, measured by libfrbx_peaks",
+                "work": f"{n_seg} segments x {seg_flop:.0f} flop (2-D FFT count)", "fit_ms": fit_mean}
+    roof.update({"hbm_frac_8B_per_cell": hbm_frac, "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_peak_kind": peaks_kind})
+    dtype = ("bf16x3 split operands, f32 accumulate (MBD transform on tcgen05); f32 elsewhere" if tc else
+             "f32")
 
     line = {"metric": metric, "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded, synth.py)", "config": cfg,
-            "dtype_note": ("f32 arithmetic; the window-tree MBD transform runs on the tensor cores as "
-                           "three BF16 products of split operands with f32 accumulation "
-                           "(f32-equivalent, about 1e-5 relative)") if stages["tree_tensor"] > 0 else "f32 arithmetic",
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic (seeded, synth.py)", "config": cfg,
+            "dtype_note": ("three BF16 products of split operands (A_hi W_hi + A_hi W_lo + A_lo W_hi) with f32 "
+                           "accumulation: about 2^-16 relative per product, measured <= 1e-5 relative on |G|; "
+                           "the argmax key keeps |G|^2 to 2^-17") if tc else "f32 arithmetic",
             "e2e": {"value": world * cells / (e2e / 1e3), "unit": "cells/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e},
-            "gpu_launches": launches, "roofline": roof, "clocks": clocks,
+            "gpu_launches": launches, "roofline": roof, "clocks": clocks, "peaks_measured": own,
             "stages_ms": stages, "segments_per_step": n_seg,
             "pulses": int(out["counts"]["pulses"]), "groups": int(out["counts"]["groups"])}
     # the tensor-core forms (MBD transform as a BF16 / FP8 DFT-GEMM on tcgen05), same workload
@@ -456,14 +474,16 @@ def main():
                 vms = max_over_ranks(v0.elapsed_time(v1) / vsteps)
                 gflops = n_seg * gemm_flops_per_segment(wl.n_chan, h.Ls, h.Lm)
                 vach = gflops / (statistics.mean(vfit) / 1e3) / 1e12
-                # the measured BF16 peak; FP8 dense tensor rate is twice BF16's (nominal ratio)
-                vpeak = peaks["bf16_tflops_sustained"] * (2.0 if vk == 5 else 1.0)
+                # sustained dense MMA rate of the operands' own type: BF16 from MEASURED_PEAKS.json,
+                # E4M3 from this GPU's own probe (libfrbx_peaks)
+                vpeak = own["fp8_mma_sustained"] if vk == 5 else peaks["bf16_tflops_sustained"]
                 line_variants[vname] = {
                     "value": world * cells / (vms / 1e3), "unit": "cells/s", "ms_per_step": vms, "steps": vsteps,
                     "dtype": vdt,
                     "roofline": {"bound": "tensor", "kernel": "k_fit_mma", "achieved": vach, "peak": vpeak,
                                  "unit": "TFLOP/s", "frac": vach / vpeak, "traffic": None,
-                                 "peak_kind": peaks_kind + " sustained bf16" + (" x 2 (fp8 nominal ratio)" if vk == 5 else ""),
+                                 "peak_kind": ("this GPU's sustained E4M3 tcgen05 rate (libfrbx_peaks)" if vk == 5
+                                               else peaks_kind + " sustained bf16"),
                                  "work": f"{n_seg} segments x {gemm_flops_per_segment(wl.n_chan, h.Ls, h.Lm):.0f} flop "
                                          "(dense DFT-GEMM of the MBD transform)",
                                  "fit_ms": statistics.mean(vfit)},

@@ -335,10 +335,14 @@ int frbx_last_stage_times(const frbx_handle *h, double *ms_out, int32_t n);
  * that loads it, held until the process exits.  A call needs, rounded up to 256 bytes per
  * piece, about 4 n_dm n_chan n_point + 16 n_seg + 17 n_chan n_point + 8 (Ls + Lm) bytes;
  * a call that would need more returns FRBX_EINVAL without running anything.
- * The first call on a device looks the array up (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  Every call on a device shares
- * the array and it keeps the last call's contents: calls that overlap on the GPU (other
- * streams, other host threads) race and must be serialised by the caller.
+ * Every call looks the array's device address up (cudaGetSymbolAddress) with the caller's
+ * device current.  The first call on a device also makes the CUDA driver load the library's
+ * device code there (lazy module loading, the default), and that load backs the 16 MiB array
+ * with device memory: a caller that reserves device memory up front should make one call at
+ * start-up (n_seg = 0 is enough) and should make it before any stream capture.  Later calls
+ * allocate nothing.  Every call on a device shares the array and it keeps the last call's
+ * contents (each call rewrites what it reads): calls that overlap on the GPU (other streams,
+ * other host threads) race and must be serialised by the caller.
  * Returns after the work on cuda_stream has finished.
  * Errors: FRBX_EINVAL (bad argument, a row reading outside the cube, scratch too small),
  * FRBX_EUNSUPPORTED, FRBX_ECUDA.
@@ -441,6 +445,41 @@ int frbx_search_batch(frbx_batch *b, const frbx_scan *scans, int32_t n_scans, co
 
 /* Number of kernel launches issued by the last frbx_search / frbx_fit_segments call. */
 int64_t frbx_last_launch_count(const frbx_handle *h);
+
+/*
+ * Per-handle resource and robustness limits.  The paper has no counterpart; these control how
+ * the library runs the method, never what it computes.  Zero in a field means its default.
+ *  tree_chunk_bytes   window-tree fits (kernels 4 and 6; frbx_search): device bytes of one of the
+ *                     two scratch sets that the chunked SBD / MBD passes alternate between.
+ *                     Default: a quarter of the free device memory, at most 16 GiB.  A small value
+ *                     gives more chunks and the same results.
+ *  wait_cycles        limit, in SM clock cycles, of every pipeline wait inside the tensor-core
+ *                     kernels (kernels 3, 5 and 6).  Default 2e9.  When a wait runs out the call
+ *                     returns FRBX_ETIMEOUT.  The waits that drain copies and MMAs still in
+ *                     flight before a CTA exits keep the 2e9 limit, so no CTA leaves work behind.
+ *  scratch_cap_bytes  cap on the device scratch the handle holds (the buffers it grows on demand;
+ *                     the constant tables of frbx_create are not counted).  Default: no cap.  A
+ *                     call that would grow the scratch past the cap returns FRBX_ENOMEM.
+ *  hold_producers     test aid, 0 = off.  The producer roles of the tensor-core kernels issue
+ *                     nothing, so the consumers' bounded waits run out: the call returns
+ *                     FRBX_ETIMEOUT without any fault, nothing is left in flight and the handle
+ *                     stays usable.  It exists so that tests can exercise the timeout path.
+ * A call that fails returns only after the work it queued has finished.
+ * frbx_set_limits(h, NULL) restores the defaults.  Errors: FRBX_EINVAL (negative field).
+ */
+typedef struct frbx_limits {
+  int64_t tree_chunk_bytes;
+  int64_t wait_cycles;
+  int64_t scratch_cap_bytes;
+  int32_t hold_producers;
+  int32_t reserved;
+} frbx_limits;
+
+int frbx_set_limits(frbx_handle *h, const frbx_limits *lim);
+int frbx_get_limits(const frbx_handle *h, frbx_limits *lim);
+
+/* Bytes of device scratch the handle holds now (see frbx_limits.scratch_cap_bytes). */
+int64_t frbx_scratch_bytes(const frbx_handle *h);
 
 #ifdef __cplusplus
 }

@@ -11,6 +11,9 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libfrbx.so")
+# peak-rate probes of the GPU (roofline denominators of the bench), a library of their own
+LIB_PEAKS = os.path.join(OUT_DIR, "libfrbx_peaks.so")
+PEAKS_SOURCES = ["peaks.cu"]
 SOURCES = ["frbx_api.cu", "kernels_fit.cu", "kernels_fft.cu", "kernels_mma.cu", "kernels_misc.cu", "kernels_refine.cu", "kernels_calib.cu", "kernels_tree.cu", "kernels_tree_mma.cu", "noalloc.cu", "extract.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off",
@@ -23,10 +26,11 @@ def _nvcc() -> str:
 
 
 def _stale() -> bool:
-    if not os.path.exists(LIB):
+    if not (os.path.exists(LIB) and os.path.exists(LIB_PEAKS)):
         return True
-    t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(ROOT, "include", "frbx.h")]
+    t = min(os.path.getmtime(LIB), os.path.getmtime(LIB_PEAKS))
+    inc = os.path.join(ROOT, "include")
+    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(inc, f) for f in os.listdir(inc)]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
@@ -48,11 +52,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
             raise RuntimeError(f"nvcc failed on {src}")
         return obj
 
-    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + f".{os.getpid()}.tmp"
-    subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
-    os.replace(tmp, LIB)
+    with ThreadPoolExecutor(max_workers=len(SOURCES) + len(PEAKS_SOURCES)) as ex:
+        objs = list(ex.map(compile_one, SOURCES + PEAKS_SOURCES))
+    for lib, part in ((LIB, objs[:len(SOURCES)]), (LIB_PEAKS, objs[len(SOURCES):])):
+        tmp = lib + f".{os.getpid()}.tmp"
+        subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *part, "-lcudart"])
+        os.replace(tmp, lib)
     return LIB
 
 

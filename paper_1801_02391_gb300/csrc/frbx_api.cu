@@ -47,6 +47,24 @@ cudaError_t ensure(frbx_handle::Buf &b, size_t bytes) {
   return e;
 }
 
+// The same for a handle's own scratch, counted against its scratch cap (frbx_limits): growing
+// past the cap fails as an allocation failure (FRBX_ENOMEM) and keeps the old buffer.
+cudaError_t ensure(frbx_handle *h, frbx_handle::Buf &b, size_t bytes) {
+  if (b.bytes >= bytes && b.p) return cudaSuccess;
+  const size_t want = std::max<size_t>(bytes, 256);
+  const size_t cap = (size_t)h->lim.scratch_cap_bytes;
+  if (cap > 0 && h->scratch_total - b.bytes + want > cap) return cudaErrorMemoryAllocation;
+  h->scratch_total -= b.bytes;
+  const cudaError_t e = ensure(b, want);
+  h->scratch_total += b.bytes;
+  return e;
+}
+
+// Pipeline-wait limit of the tensor-core kernels, and the limit of the waits that drain work in
+// flight before a CTA exits.
+constexpr long long kDrainCycles = 2000000000LL;
+long long wait_cycles(const frbx_handle *h) { return h->lim.wait_cycles > 0 ? h->lim.wait_cycles : kDrainCycles; }
+
 template <class T>
 cudaError_t upload(T **dst, const std::vector<T> &src) {
   cudaError_t e = cudaMalloc((void **)dst, std::max<size_t>(1, src.size()) * sizeof(T));
@@ -128,6 +146,56 @@ struct Layout {
 
 }  // namespace
 
+namespace frbx {
+
+int setup_grid(const frbx_setup *s, SetupGrid *o) {
+  if (!s || !s->f0_mhz || !o) return FRBX_EINVAL;
+  const int N = s->n_chan, J = s->n_point;
+  if (N < 1 || N > kMaxChan || J < 2 || J > kMaxPoint) return FRBX_EINVAL;
+  if (!(s->f_bw_mhz > 0) || !(s->t_ap_ms > 0) || !std::isfinite(s->f_bw_mhz) || !std::isfinite(s->t_ap_ms))
+    return FRBX_EINVAL;
+  o->N = N;
+  o->J = J;
+  o->C = N * J;
+  double fmax = 0, fmin0 = 0;
+  for (int n = 0; n < N; ++n) {
+    const double f0 = s->f0_mhz[n];
+    if (!(f0 > 0) || !std::isfinite(f0)) return FRBX_EINVAL;
+    fmin0 = n == 0 ? f0 : std::min(fmin0, f0);
+    for (int j = 0; j < J; ++j) fmax = std::max(fmax, f0 + ((double)j * s->f_bw_mhz) / (double)J);
+  }
+  o->fmin0 = fmin0;
+  o->f_ref = s->f_ref_dm_mhz != 0.0 ? s->f_ref_dm_mhz : fmax;
+  if (!(o->f_ref >= fmax)) return FRBX_EINVAL;  // a reference below the band would make negative shifts
+  // MBD grid: GCD of the channel offsets in whole kHz
+  long long off_khz[kMaxChan], gcd = 0;
+  for (int n = 0; n < N; ++n) {
+    const double v = (s->f0_mhz[n] - fmin0) * 1000.0, r = std::nearbyint(v);
+    if (std::fabs(v - r) > 1e-3) return FRBX_EINVAL;
+    off_khz[n] = (long long)r;
+    if (r != 0) gcd = std::gcd(gcd, (long long)r);
+  }
+  if (gcd == 0) gcd = (long long)std::nearbyint(s->f_bw_mhz * 1000.0);
+  if (gcd <= 0) return FRBX_EINVAL;
+  o->df_grid = (double)gcd / 1000.0;
+  int gmax = 0;
+  for (int n = 0; n < N; ++n) {
+    const long long gv = off_khz[n] / gcd;
+    if (gv > kMaxLm) return FRBX_EUNSUPPORTED;
+    o->g[n] = (int)gv;
+    gmax = std::max(gmax, (int)gv);
+  }
+  const int sp = s->sbd_pad ? s->sbd_pad : 2, mp = s->mbd_pad ? s->mbd_pad : 2;
+  if (sp < 1 || mp < 1) return FRBX_EINVAL;
+  o->Ls = sp * J;
+  o->Lm = mp * next_pow2(gmax + 1);
+  if (!is_pow2(o->Ls) || !is_pow2(o->Lm) || o->Ls > kMaxLs || o->Lm > kMaxLm || (long long)o->Ls * o->Lm > (1LL << 20))
+    return FRBX_EUNSUPPORTED;
+  return FRBX_OK;
+}
+
+}  // namespace frbx
+
 extern "C" {
 
 void frbx_default_params(frbx_params *p) {
@@ -147,84 +215,27 @@ void frbx_default_params(frbx_params *p) {
 int frbx_create(const frbx_setup *s, frbx_handle **out) {
   if (!out) return FRBX_EINVAL;
   *out = nullptr;
-  if (!s || !s->f0_mhz) return FRBX_EINVAL;
-  const int N = s->n_chan, J = s->n_point;
-  if (N < 1 || N > frbx::kMaxChan || J < 2 || J > frbx::kMaxPoint) return FRBX_EINVAL;
-  if (!(s->f_bw_mhz > 0) || !(s->t_ap_ms > 0) || !std::isfinite(s->f_bw_mhz) ||
-      !std::isfinite(s->t_ap_ms))
-    return FRBX_EINVAL;
+  frbx::SetupGrid sg;
+  const int rc = frbx::setup_grid(s, &sg);
+  if (rc != FRBX_OK) return rc;
+  const int N = sg.N, J = sg.J;
   auto *h = new frbx_handle();
   for (auto &row : h->slot_n)
     for (short &v : row) v = -1;
   h->N = N;
   h->J = J;
-  h->C = N * J;
+  h->C = sg.C;
   h->f_bw = s->f_bw_mhz;
   h->t_ap = s->t_ap_ms;
   h->f0.assign(s->f0_mhz, s->f0_mhz + N);
-  for (double v : h->f0) {
-    if (!(v > 0) || !std::isfinite(v)) {
-      delete h;
-      return FRBX_EINVAL;
-    }
-  }
-  // point frequencies f0_n + (j * f_bw) / J
   h->f.resize((size_t)h->C);
-  double fmax = 0;
   for (int n = 0; n < N; ++n)
-    for (int j = 0; j < J; ++j) {
-      const double f = h->f0[(size_t)n] + ((double)j * s->f_bw_mhz) / (double)J;
-      h->f[(size_t)n * J + j] = f;
-      fmax = std::max(fmax, f);
-    }
-  h->f_ref = s->f_ref_dm_mhz != 0.0 ? s->f_ref_dm_mhz : fmax;
-  if (!(h->f_ref >= fmax)) {
-    delete h;
-    return FRBX_EINVAL;  // a reference below the band would make negative shifts
-  }
-  // MBD grid: GCD of the channel offsets in whole kHz
-  const double fmin0 = *std::min_element(h->f0.begin(), h->f0.end());
-  std::vector<long long> off_khz((size_t)N);
-  long long gcd = 0;
-  for (int n = 0; n < N; ++n) {
-    const double o = (h->f0[(size_t)n] - fmin0) * 1000.0;
-    const double r = std::nearbyint(o);
-    if (std::fabs(o - r) > 1e-3) {
-      delete h;
-      return FRBX_EINVAL;
-    }
-    off_khz[(size_t)n] = (long long)r;
-    if (r != 0) gcd = std::gcd(gcd, (long long)r);
-  }
-  if (gcd == 0) gcd = (long long)std::nearbyint(s->f_bw_mhz * 1000.0);
-  if (gcd <= 0) {
-    delete h;
-    return FRBX_EINVAL;
-  }
-  h->df_grid = (double)gcd / 1000.0;
-  h->g.resize((size_t)N);
-  int gmax = 0;
-  for (int n = 0; n < N; ++n) {
-    const long long gv = off_khz[(size_t)n] / gcd;
-    if (gv > frbx::kMaxLm) {
-      delete h;
-      return FRBX_EUNSUPPORTED;
-    }
-    h->g[(size_t)n] = (int)gv;
-    gmax = std::max(gmax, (int)gv);
-  }
-  const int sp = s->sbd_pad ? s->sbd_pad : 2, mp = s->mbd_pad ? s->mbd_pad : 2;
-  if (sp < 1 || mp < 1) {
-    delete h;
-    return FRBX_EINVAL;
-  }
-  h->Ls = sp * J;
-  h->Lm = mp * next_pow2(gmax + 1);
-  if (!is_pow2(h->Ls) || !is_pow2(h->Lm) || h->Ls > frbx::kMaxLs || h->Lm > frbx::kMaxLm ||
-      (long long)h->Ls * h->Lm > (1LL << 20)) {
-    delete h;
-    return FRBX_EUNSUPPORTED;
-  }
+    for (int j = 0; j < J; ++j) h->f[(size_t)n * J + j] = h->f0[(size_t)n] + ((double)j * s->f_bw_mhz) / (double)J;
+  h->f_ref = sg.f_ref;
+  h->df_grid = sg.df_grid;
+  h->g.assign(sg.g, sg.g + N);
+  h->Ls = sg.Ls;
+  h->Lm = sg.Lm;
   h->J1 = (J + 31) / 32;
   // weight x calibration rotation exp(-i[2 pi (f_j - f_bw/2) dtau0_n + dphi0_n]) (Eq. 5)
   const double two_pi = 6.283185307179586476925286766559;
@@ -471,6 +482,27 @@ int64_t frbx_series_layout(int32_t T, const int32_t *windows, int32_t n_win, int
 
 int64_t frbx_last_launch_count(const frbx_handle *h) { return h ? h->launches : -1; }
 
+int frbx_set_limits(frbx_handle *h, const frbx_limits *lim) {
+  if (!h) return FRBX_EINVAL;
+  if (!lim) {
+    h->lim = frbx_limits{};
+    return FRBX_OK;
+  }
+  if (lim->tree_chunk_bytes < 0 || lim->wait_cycles < 0 || lim->scratch_cap_bytes < 0 || lim->hold_producers < 0)
+    return fail(h, FRBX_EINVAL, "limits must be >= 0");
+  h->lim = *lim;
+  h->lim.reserved = 0;
+  return FRBX_OK;
+}
+
+int frbx_get_limits(const frbx_handle *h, frbx_limits *lim) {
+  if (!h || !lim) return FRBX_EINVAL;
+  *lim = h->lim;
+  return FRBX_OK;
+}
+
+int64_t frbx_scratch_bytes(const frbx_handle *h) { return h ? (int64_t)h->scratch_total : -1; }
+
 }  // extern "C"
 
 namespace {
@@ -480,9 +512,9 @@ int run_shift_table(frbx_handle *h, const double *dm, int n_dm, std::vector<int>
                     cudaStream_t st) {
   for (int d = 0; d < n_dm; ++d)
     if (!(dm[d] >= 0) || !std::isfinite(dm[d])) return fail(h, FRBX_EINVAL, "DM trials must be finite and >= 0");
-  FRBX_CK(h, ensure(h->small, sizeof(double) * (size_t)n_dm + 4096));
-  FRBX_CK(h, ensure(h->dk, sizeof(int) * (size_t)n_dm * h->C));
-  FRBX_CK(h, ensure(h->dk_max, sizeof(int) * (size_t)n_dm));
+  FRBX_CK(h, ensure(h, h->small, sizeof(double) * (size_t)n_dm + 4096));
+  FRBX_CK(h, ensure(h, h->dk, sizeof(int) * (size_t)n_dm * h->C));
+  FRBX_CK(h, ensure(h, h->dk_max, sizeof(int) * (size_t)n_dm));
   double *d_dm = (double *)h->small.p;
   FRBX_CK(h, cudaMemcpyAsync(d_dm, dm, sizeof(double) * n_dm, cudaMemcpyHostToDevice, st));
   FRBX_CK(h, frbx::launch_shift_table(h->d_f, h->C, h->f_ref, d_dm, n_dm, h->t_ap, (int *)h->dk.p,
@@ -554,7 +586,7 @@ int check_vis(frbx_handle *h, const void *vis, int vis_on_device, int n_bl, int 
     *dvis = (const float2 *)vis;
     return FRBX_OK;
   }
-  FRBX_CK(h, ensure(h->vis, bytes));
+  FRBX_CK(h, ensure(h, h->vis, bytes));
   FRBX_CK(h, cudaMemcpyAsync(h->vis.p, vis, bytes, cudaMemcpyHostToDevice, st));
   *dvis = (const float2 *)h->vis.p;
   return FRBX_OK;
@@ -600,8 +632,10 @@ int run_fit_mma(frbx_handle *h, const FitArgs &a, int n_bl, bool list_mode, long
   mm.spt = 128 / h->Ls;
   mm.n_valid = n_valid;
   mm.n_items = list_mode ? 0 : (long long)n_bl * ((a.T + a.TT - 1) / a.TT) * a.n_dm;
-  mm.timeout = 2000000000LL;
-  FRBX_CK(h, ensure(h->errflag, sizeof(int)));
+  mm.timeout = wait_cycles(h);
+  mm.drain_timeout = kDrainCycles;
+  mm.hold = h->lim.hold_producers ? 1 : 0;
+  FRBX_CK(h, ensure(h, h->errflag, sizeof(int)));
   FRBX_CK(h, cudaMemsetAsync(h->errflag.p, 0, sizeof(int), st));
   mm.err = (int *)h->errflag.p;
   cudaError_t e = frbx::launch_fit_mma(a, mm, n_bl, list_mode, st, &h->launches);
@@ -617,9 +651,9 @@ int run_fit_mma(frbx_handle *h, const FitArgs &a, int n_bl, bool list_mode, long
 // Normalise + threshold + ordered events of n_series series (baselines or combos).
 int run_stats(frbx_handle *h, StatsArgs sa, cudaStream_t st, std::vector<frbx_event> *ev) {
   const size_t ns = (size_t)sa.n_series * sa.n_dm * sa.n_win;
-  FRBX_CK(h, ensure(h->stats, sizeof(double) * 2 * ns));
-  FRBX_CK(h, ensure(h->counts, sizeof(int) * (ns + 1)));
-  FRBX_CK(h, ensure(h->offsets, sizeof(long long) * (ns + 1)));
+  FRBX_CK(h, ensure(h, h->stats, sizeof(double) * 2 * ns));
+  FRBX_CK(h, ensure(h, h->counts, sizeof(int) * (ns + 1)));
+  FRBX_CK(h, ensure(h, h->offsets, sizeof(long long) * (ns + 1)));
   sa.mean_std = (double *)h->stats.p;
   sa.counts = (int *)h->counts.p;
   sa.offsets = (long long *)h->offsets.p;
@@ -630,7 +664,7 @@ int run_stats(frbx_handle *h, StatsArgs sa, cudaStream_t st, std::vector<frbx_ev
   FRBX_CK(h, cudaStreamSynchronize(st));
   ev->resize((size_t)total);
   if (total == 0) return FRBX_OK;
-  FRBX_CK(h, ensure(h->events, sizeof(frbx_event) * (size_t)total));
+  FRBX_CK(h, ensure(h, h->events, sizeof(frbx_event) * (size_t)total));
   sa.events = (frbx_event *)h->events.p;
   FRBX_CK(h, frbx::launch_events(sa, st, &h->launches));
   FRBX_CK(h, cudaMemcpyAsync(ev->data(), sa.events, sizeof(frbx_event) * (size_t)total,
@@ -699,7 +733,9 @@ void plan_tree(const frbx_handle *h, const FitArgs &a, int nlev, const int32_t *
     t.n_qb = h->Lm / 32;
     t.log2Lm = a.log2Lm;
     t.err = (int *)h->errflag.p;
-    t.timeout = 2000000000LL;
+    t.timeout = wait_cycles(h);
+    t.drain_timeout = kDrainCycles;
+    t.hold = h->lim.hold_producers ? 1 : 0;
     t.yt_series = (size_t)T * t.tile_bytes;
     t.y_series = t.yt_series / sizeof(float2);
   }
@@ -792,9 +828,10 @@ int run_fit_tree(frbx_handle *h, const FitArgs &a, int nlev, bool mma, const int
                  const std::vector<int> &dkm, int n_bl, int T, int n_dm, const int *d_tab, int S_tot, cudaStream_t st) {
   size_t free_b = 0, total_b = 0;
   FRBX_CK(h, cudaMemGetInfo(&free_b, &total_b));
-  const size_t budget = std::min<size_t>((size_t)16 << 30, (free_b + h->ytree.bytes) / 4);
+  const size_t budget = h->lim.tree_chunk_bytes > 0 ? (size_t)h->lim.tree_chunk_bytes
+                                                    : std::min<size_t>((size_t)16 << 30, (free_b + h->ytree.bytes) / 4);
   if (mma) {
-    FRBX_CK(h, ensure(h->errflag, sizeof(int)));
+    FRBX_CK(h, ensure(h, h->errflag, sizeof(int)));
     FRBX_CK(h, cudaMemsetAsync(h->errflag.p, 0, sizeof(int), st));
   }
   TreeRun r;
@@ -802,7 +839,7 @@ int run_fit_tree(frbx_handle *h, const FitArgs &a, int nlev, bool mma, const int
   int rc = tree_prepare(h);
   if (rc) return rc;
   const size_t ser_bytes = (sizeof(int2) * std::max<size_t>(r.ser.size(), 1) + 255) & ~(size_t)255;
-  FRBX_CK(h, ensure(h->ytree, ser_bytes + r.need()));
+  FRBX_CK(h, ensure(h, h->ytree, ser_bytes + r.need()));
   int2 *d_ser = (int2 *)h->ytree.p;
   if (!r.ser.empty())
     FRBX_CK(h, cudaMemcpyAsync(d_ser, r.ser.data(), sizeof(int2) * r.ser.size(), cudaMemcpyHostToDevice, st));
@@ -831,7 +868,7 @@ int finish_search(frbx_handle *h, const frbx_seg *series, int n_bl, int T, const
     if (res->series_on_device) {
       pn = res->pnorm;
     } else {
-      FRBX_CK(h, ensure(h->pnorm, sizeof(float) * n_series_el));
+      FRBX_CK(h, ensure(h, h->pnorm, sizeof(float) * n_series_el));
       pn = (float *)h->pnorm.p;
     }
     FRBX_CK(h, cudaMemsetAsync(pn, 0, sizeof(float) * n_series_el, st));
@@ -855,7 +892,7 @@ int finish_search(frbx_handle *h, const frbx_seg *series, int n_bl, int T, const
   if (rc) return rc;
   FRBX_CK(h, cudaEventRecord(h->ev[4], st));
   if (p.n_combo > 0) {
-    FRBX_CK(h, ensure(h->masks, sizeof(uint64_t) * (size_t)p.n_combo));
+    FRBX_CK(h, ensure(h, h->masks, sizeof(uint64_t) * (size_t)p.n_combo));
     FRBX_CK(h, cudaMemcpyAsync(h->masks.p, p.combos, sizeof(uint64_t) * p.n_combo, cudaMemcpyHostToDevice, st));
     sa.masks = (const unsigned long long *)h->masks.p;
     sa.n_series = p.n_combo;
@@ -956,10 +993,10 @@ extern "C" int frbx_shift_table(frbx_handle *h, const double *dm, int32_t n_dm, 
   return FRBX_OK;
 }
 
-extern "C" int frbx_fit_segments(frbx_handle *h, const void *vis, int32_t vis_on_device, int32_t n_bl,
-                                 int32_t T, const double *dm, int32_t n_dm, const int32_t *segs,
-                                 int64_t n_seg, const frbx_params *params, frbx_seg *out,
-                                 void *cuda_stream) {
+static int fit_segments_impl(frbx_handle *h, const void *vis, int32_t vis_on_device, int32_t n_bl,
+                             int32_t T, const double *dm, int32_t n_dm, const int32_t *segs,
+                             int64_t n_seg, const frbx_params *params, frbx_seg *out,
+                             void *cuda_stream) {
   if (!h) return FRBX_EINVAL;
   h->launches = 0;
   cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -983,8 +1020,8 @@ extern "C" int frbx_fit_segments(frbx_handle *h, const void *vis, int32_t vis_on
       return fail(h, FRBX_EINVAL, "segment row " + std::to_string(i) + " reads outside the cube");
   }
   if (n_seg == 0) return FRBX_OK;
-  FRBX_CK(h, ensure(h->seglist, sizeof(int32_t) * 4 * (size_t)n_seg));
-  FRBX_CK(h, ensure(h->series, sizeof(frbx_seg) * (size_t)n_seg));
+  FRBX_CK(h, ensure(h, h->seglist, sizeof(int32_t) * 4 * (size_t)n_seg));
+  FRBX_CK(h, ensure(h, h->series, sizeof(frbx_seg) * (size_t)n_seg));
   FRBX_CK(h, cudaMemcpyAsync(h->seglist.p, segs, sizeof(int32_t) * 4 * (size_t)n_seg, cudaMemcpyHostToDevice, st));
   if (p.kernel == 4 || p.kernel == 6) p.kernel = 0;  // explicit segment lists have no window structure to exploit
   fill_fit_tables(h, &a, dvis, T, n_dm);
@@ -1005,10 +1042,10 @@ extern "C" int frbx_fit_segments(frbx_handle *h, const void *vis, int32_t vis_on
   return FRBX_OK;
 }
 
-extern "C" int frbx_search(frbx_handle *h, const void *vis, int32_t vis_on_device, int32_t n_bl,
-                           int32_t T, const double *dm, int32_t n_dm, const int32_t *windows,
-                           int32_t n_win, const frbx_params *params, frbx_results *res,
-                           void *cuda_stream) {
+static int search_impl(frbx_handle *h, const void *vis, int32_t vis_on_device, int32_t n_bl,
+                       int32_t T, const double *dm, int32_t n_dm, const int32_t *windows,
+                       int32_t n_win, const frbx_params *params, frbx_results *res,
+                       void *cuda_stream) {
   if (!h) return FRBX_EINVAL;
   h->launches = 0;
   h->err.clear();
@@ -1062,11 +1099,11 @@ extern "C" int frbx_search(frbx_handle *h, const void *vis, int32_t vis_on_devic
   tab.insert(tab.end(), L.win_step.begin(), L.win_step.end());
   tab.resize(3 * frbx::kMaxWin, 0);
   tab.insert(tab.end(), L.n_valid.begin(), L.n_valid.end());
-  FRBX_CK(h, ensure(h->small, sizeof(int) * tab.size() + 4096));
+  FRBX_CK(h, ensure(h, h->small, sizeof(int) * tab.size() + 4096));
   int *d_tab = (int *)h->small.p;
   FRBX_CK(h, cudaMemcpyAsync(d_tab, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice, st));
   const size_t n_series_el = (size_t)n_bl * n_dm * L.S_tot;
-  FRBX_CK(h, ensure(h->series, sizeof(frbx_seg) * n_series_el));
+  FRBX_CK(h, ensure(h, h->series, sizeof(frbx_seg) * n_series_el));
 
   // fit every segment
   fill_fit_tables(h, &a, dvis, T, n_dm);
@@ -1105,6 +1142,37 @@ extern "C" int frbx_search(frbx_handle *h, const void *vis, int32_t vis_on_devic
   FRBX_CK(h, cudaEventRecord(h->ev[3], st));
 
   return finish_search(h, (const frbx_seg *)h->series.p, n_bl, T, dm, n_dm, n_win, L, d_tab, p, res, st);
+}
+
+namespace {
+// After a failed call: wait for the work it queued (caller stream and the library's own
+// streams), so the caller may release its buffers, and clear a non-sticky CUDA error.
+void settle(frbx_handle *h, cudaStream_t st) {
+  cudaStreamSynchronize(st);
+  for (cudaStream_t x : h->tree_st)
+    if (x) cudaStreamSynchronize(x);
+  cudaGetLastError();
+}
+}  // namespace
+
+extern "C" int frbx_fit_segments(frbx_handle *h, const void *vis, int32_t vis_on_device, int32_t n_bl,
+                                 int32_t T, const double *dm, int32_t n_dm, const int32_t *segs,
+                                 int64_t n_seg, const frbx_params *params, frbx_seg *out,
+                                 void *cuda_stream) {
+  if (!h) return FRBX_EINVAL;
+  const int rc = fit_segments_impl(h, vis, vis_on_device, n_bl, T, dm, n_dm, segs, n_seg, params, out, cuda_stream);
+  if (rc != FRBX_OK) settle(h, (cudaStream_t)cuda_stream);
+  return rc;
+}
+
+extern "C" int frbx_search(frbx_handle *h, const void *vis, int32_t vis_on_device, int32_t n_bl,
+                           int32_t T, const double *dm, int32_t n_dm, const int32_t *windows,
+                           int32_t n_win, const frbx_params *params, frbx_results *res,
+                           void *cuda_stream) {
+  if (!h) return FRBX_EINVAL;
+  const int rc = search_impl(h, vis, vis_on_device, n_bl, T, dm, n_dm, windows, n_win, params, res, cuda_stream);
+  if (rc != FRBX_OK && rc != FRBX_ETRUNC) settle(h, (cudaStream_t)cuda_stream);
+  return rc;
 }
 
 extern "C" int frbx_extract_events(const frbx_event *events, int64_t n_events, int32_t n_series,
@@ -1238,7 +1306,7 @@ extern "C" int frbx_refine_adjoint(frbx_handle *h, const void *vis_dev, int32_t 
   int rc = refine_common(h, vis_dev, n_bl, T, params_dev, width_dev, n_cand, &r);
   if (rc) return rc;
   if (n_cand > 0 && (!g_dev || !dpower_dev || !dparams_dev)) return fail(h, FRBX_EINVAL, "missing input or output");
-  FRBX_CK(h, ensure(h->refine, sizeof(float) * 2 * (size_t)n_cand * n_bl + 16));
+  FRBX_CK(h, ensure(h, h->refine, sizeof(float) * 2 * (size_t)n_cand * n_bl + 16));
   r.g = const_cast<float *>(g_dev);
   r.dpower = dpower_dev;
   r.dparams = dparams_dev;
@@ -1270,7 +1338,7 @@ extern "C" int frbx_calibrate(frbx_handle *h, const void *vis, int32_t vis_on_de
   const size_t o_xs = take(16 * (size_t)n_bl * C), o_xc = take(8 * (size_t)n_bl * C), o_w = take(8 * (size_t)C),
                o_dk = take(4 * (size_t)C), o_rows = take(16 * (size_t)n_bl), o_fit = take(8 * (size_t)n_bl),
                o_sm = take(16 * (size_t)n_bl), o_d = take(8 * (size_t)n_bl * N), o_p = take(8 * (size_t)n_bl * N);
-  FRBX_CK(h, ensure(h->calib, off));
+  FRBX_CK(h, ensure(h, h->calib, off));
   unsigned char *b = (unsigned char *)h->calib.p;
   FRBX_CK(h, frbx::launch_cal_sum(dvis, T, C, n_bl, k0, l, h->d_wrot, (double2 *)(b + o_xs), (float2 *)(b + o_xc),
                                   (float2 *)(b + o_w), st, &h->launches));
@@ -1616,7 +1684,7 @@ extern "C" int frbx_search_batch(frbx_batch *b, const frbx_scan *scans, int32_t 
   int64_t tree_launches = 0;
   if (n_tree_setups) {
     for (size_t g = 0; g < setups.size(); ++g)
-      if (tree_lev[g] >= 0) FRBX_BCK(b, ensure(setups[g]->errflag, sizeof(int)));
+      if (tree_lev[g] >= 0) FRBX_BCK(b, ensure(setups[g], setups[g]->errflag, sizeof(int)));
     size_t free_b = 0, total_b = 0;
     FRBX_BCK(b, cudaMemGetInfo(&free_b, &total_b));
     for (int i = 0; i < n_scans; ++i) {
@@ -1624,7 +1692,9 @@ extern "C" int frbx_search_batch(frbx_batch *b, const frbx_scan *scans, int32_t 
       if (tree_lev[(size_t)g] < 0) continue;
       frbx_handle *h = setups[(size_t)g];
       const size_t budget =
-          std::min<size_t>((size_t)16 << 30, (free_b + h->ytree.bytes) / (4 * n_tree_setups));
+          h->lim.tree_chunk_bytes > 0
+              ? (size_t)h->lim.tree_chunk_bytes
+              : std::min<size_t>((size_t)16 << 30, (free_b + h->ytree.bytes) / (4 * n_tree_setups));
       FitArgs a = fit_args(g, 1024);
       fill_fit_tables(h, &a, (const float2 *)scans[i].vis_dev, scans[i].T, n_dm);
       a.win_off = d_tab + woff_at[(size_t)i];
@@ -1642,7 +1712,7 @@ extern "C" int frbx_search_batch(frbx_batch *b, const frbx_scan *scans, int32_t 
     for (size_t g = 0; g < setups.size(); ++g) {
       if (tree_lev[g] < 0) continue;
       frbx_handle *h = setups[g];
-      if (ensure(h->errflag, sizeof(int)) != cudaSuccess || ensure(h->ytree, need_h[g]) != cudaSuccess ||
+      if (ensure(h, h->errflag, sizeof(int)) != cudaSuccess || ensure(h, h->ytree, need_h[g]) != cudaSuccess ||
           tree_prepare(h) != FRBX_OK) {
         cudaGetLastError();
         return bfail(b, FRBX_ENOMEM, "setup " + std::to_string(g) + ": window-tree scratch");
@@ -1766,7 +1836,7 @@ extern "C" int frbx_search_batch(frbx_batch *b, const frbx_scan *scans, int32_t 
     h->launches = 0;
     h->tree_chunks = 0;
     int rc = FRBX_OK;
-    if (ensure(h->small, sizeof(int) * t2.size() + 4096) != cudaSuccess ||
+    if (ensure(h, h->small, sizeof(int) * t2.size() + 4096) != cudaSuccess ||
         cudaMemcpyAsync(h->small.p, t2.data(), sizeof(int) * t2.size(), cudaMemcpyHostToDevice, st) != cudaSuccess) {
       cudaGetLastError();
       return bfail(b, FRBX_ECUDA, "scan " + std::to_string(i) + ": table upload failed");

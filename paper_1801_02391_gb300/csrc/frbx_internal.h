@@ -20,6 +20,19 @@ constexpr int kMaxWin = 16;
 constexpr int kMaxBl = 64;
 constexpr int kFitThreads = 256;
 
+// Setup scalars shared by frbx_create and frbx_fit_segments_noalloc (host code, no allocation):
+// the checked setup, the reference frequency of Eq. 1 (f_ref), the MBD grid of Eq. 5 (df_grid
+// = GCD of the channel offsets in whole kHz, g_n = offset / df_grid) and the grid sizes
+// Ls = sbd_pad J, Lm = mbd_pad nextpow2(max g_n + 1).  Point frequencies are
+// f0_n + (j f_bw) / J, evaluated in that order.
+struct SetupGrid {
+  int N, J, C, Ls, Lm;
+  double f_ref, df_grid, fmin0;
+  int g[kMaxChan];
+};
+// FRBX_OK, or FRBX_EINVAL / FRBX_EUNSUPPORTED for a setup the library rejects.
+int setup_grid(const frbx_setup *s, SetupGrid *out);
+
 // One scan of a batched fit: its cube, output series, valid-segment table and first work item.
 struct BatchScan {
   const float2 *vis;       // [n_bl][T][C]
@@ -88,7 +101,9 @@ struct MmaArgs {
   long long n_valid;       // segments to fit
   long long n_items;       // implicit layout: n_bl * ceil(T / TT) * n_dm work items
   int *err;                // device flag, set to FRBX_ETIMEOUT when a bounded wait gives up
-  long long timeout;       // clock cycles per wait
+  long long timeout;       // clock cycles per pipeline wait
+  long long drain_timeout; // clock cycles per wait that drains work in flight before exit
+  int hold;                // test aid: the producers issue nothing, so the pipeline waits run out
   int fp8;                 // 1: A and B in E4M3 (kind::f8f6f4), A scaled per segment
 };
 bool mma_supported(int Ls, int Lm, int N, int J);
@@ -161,7 +176,9 @@ struct TreeArgs {
   int n_qb;                // Lm / 32
   int log2Lm;
   int *err;                // set to FRBX_ETIMEOUT when a bounded wait of k_tree_mma gives up
-  long long timeout;       // clock cycles per wait
+  long long timeout;       // clock cycles per pipeline wait
+  long long drain_timeout; // clock cycles per wait that drains copies / MMAs in flight before exit
+  int hold;                // test aid: the loader issues no copies, so the pipeline waits run out
   int n_abuf;              // A-tile ring depth of k_tree_mma (set by its launcher)
   int n_sanc;              // window-tree anchor levels of k_tree_mma in shared memory (set by its launcher)
 };
@@ -258,6 +275,8 @@ struct frbx_handle {
     void *p = nullptr;
     size_t bytes = 0;
   };
+  frbx_limits lim{};          // frbx_set_limits (all zero = defaults)
+  size_t scratch_total = 0;   // bytes held by the Bufs below
   Buf vis, dk, dk_max, series, pnorm, stats, counts, offsets, events, small, seglist, masks, errflag, refine, calib,
       ytree;
 };

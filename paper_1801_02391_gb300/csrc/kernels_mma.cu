@@ -217,7 +217,8 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
     ItemTab &tab = tabs[g];
     float2 *X = reinterpret_cast<float2 *>(smem + L.x_off) + (size_t)g * N * L.xs;
     long long i = 0;  // CTA-local tile counter
-    for (long long item = blockIdx.x; item < n_items; item += gridDim.x) {
+    const long long n_prod = mm.hold ? 0 : n_items;  // test aid: with hold, the producers issue nothing
+    for (long long item = blockIdx.x; item < n_prod; item += gridDim.x) {
       if (gtid == 0) {
         if (list) {
           tab.nseg = (int)min((long long)kListItem, mm.n_valid - item * kListItem);
@@ -406,7 +407,7 @@ __global__ void __launch_bounds__(kMmaThreads, 1)
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                    ::"r"(su32(&bar_drain)) : "memory");
     __syncwarp();
-    if (!__all_sync(0xffffffffu, mbar_wait(&bar_drain, 0, nullptr, mm.timeout))) *abortp = 1;
+    if (!__all_sync(0xffffffffu, mbar_wait(&bar_drain, 0, nullptr, mm.drain_timeout))) *abortp = 1;
   } else {
     // ================= epilogue: |G|^2 and the grid maximum =================
     const int ew = warp - kEpiWarp0;           // 0..7

@@ -209,8 +209,9 @@ __global__ void __launch_bounds__((kEpi + 2) * 32, 1) k_tree_mma(const __grid_co
     if (lane == 0) {
       const unsigned char *src = t.Yt + (size_t)s * t.yt_series + (size_t)kb * t.tile_bytes;
       int issued = 0;
+      const int n_load = t.hold ? 0 : n_ap;  // test aid: with hold, no copy is issued
       // ring position b and the parity of its current use, advanced without a division
-      for (int i = 0, b = 0, ph = 0; i < n_ap; ++i) {
+      for (int i = 0, b = 0, ph = 0; i < n_load; ++i) {
         if (!tc::mbar_wait(&bar_aempty[b], (uint32_t)ph ^ 1u, abortp, t.timeout)) {
           *abortp = 1;
           break;
@@ -226,7 +227,7 @@ __global__ void __launch_bounds__((kEpi + 2) * 32, 1) k_tree_mma(const __grid_co
       }
       // every copy issued has landed before the CTA can leave (bounded; ignores the abort flag)
       for (int i = max(0, issued - nbuf); i < issued; ++i)
-        if (!tc::mbar_wait(&bar_afull[i % nbuf], (uint32_t)(i / nbuf) & 1, nullptr, t.timeout)) *abortp = 1;
+        if (!tc::mbar_wait(&bar_afull[i % nbuf], (uint32_t)(i / nbuf) & 1, nullptr, t.drain_timeout)) *abortp = 1;
     }
     __syncwarp();
   } else if (warp == kMmaWarp) {
@@ -280,7 +281,7 @@ __global__ void __launch_bounds__((kEpi + 2) * 32, 1) k_tree_mma(const __grid_co
       // drain: a last commit lands only when every MMA this thread issued has completed
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                    ::"r"(tc::su32(&bar_drain)) : "memory");
-      if (!tc::mbar_wait(&bar_drain, 0, nullptr, t.timeout)) *abortp = 1;
+      if (!tc::mbar_wait(&bar_drain, 0, nullptr, t.drain_timeout)) *abortp = 1;
     }
     __syncwarp();
   } else {

@@ -3,8 +3,6 @@
 // one file-scope __device__ array of fixed size; see include/frbx.h for the contract.
 #include <cmath>
 #include <cstring>
-#include <mutex>
-#include <numeric>
 
 #include "frbx_internal.h"
 
@@ -13,29 +11,14 @@ namespace frbx {
 namespace {
 
 constexpr size_t kScratchBytes = size_t(16) << 20;  // 16 MiB on every device that loads the library
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-std::mutex g_addr_mu;
-void *g_addr[kMaxDevices] = {};
-
-// Device address of the scratch array for the current device (looked up once per device).
-cudaError_t scratch_address(void **out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_addr_mu);
-  if (!g_addr[dev]) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_addr[dev] = p;
-  }
-  *out = g_addr[dev];
-  return cudaSuccess;
-}
+// Device address of the scratch array on the current device.  Looked up on every call: the
+// lookup allocates nothing once the library's module is loaded on the device (the first call
+// there loads it), and a cached pointer would go stale after cudaDeviceReset or in another
+// context.
+cudaError_t scratch_address(void **out) { return cudaGetSymbolAddress(out, g_noalloc_scratch); }
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
@@ -44,6 +27,9 @@ struct SetupParams {
   double f_bw, f_ref;
   int g[kMaxChan];
 };
+
+__device__ __forceinline__ double dmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
 
 // Point frequencies (FP64, the order of frbx_create), weight x calibration rotation, and the
 // SBD / MBD twiddle tables, computed on the device from the copied setup arrays.
@@ -58,19 +44,21 @@ __global__ void k_noalloc_tables(SetupParams sp, const double *f0, const double 
     f[i] = __dadd_rn(f0[n], fj);
     const bool used = j > 0 && !(have_flag && flag[i]);
     const double dt = have_dtau ? dtau[n] : 0.0, dp = have_dphi ? dphi[n] : 0.0;
-    const double ph = two_pi * (fj - sp.f_bw / 2.0) * dt * 1e-3 + dp;
+    // the calibration phase of Eq. 5 in frbx_create's order, each step rounded on its own
+    // (no contraction): ((2 pi (f_j - f_bw / 2)) dtau) 1e-3 + dphi
+    const double ph = dadd(dmul(dmul(dmul(two_pi, __dsub_rn(fj, __ddiv_rn(sp.f_bw, 2.0))), dt), 1e-3), dp);
     double sn, cs;
     sincos(ph, &sn, &cs);
     wrot[i] = used ? make_float2((float)cs, (float)-sn) : make_float2(0.f, 0.f);
   }
   if (i < sp.Ls) {
     double sn, cs;
-    sincos(two_pi * i / sp.Ls, &sn, &cs);
+    sincos(__ddiv_rn(dmul(two_pi, (double)i), (double)sp.Ls), &sn, &cs);
     tws[i] = make_float2((float)cs, (float)-sn);
   }
   if (i < sp.Lm) {
     double sn, cs;
-    sincos(two_pi * i / sp.Lm, &sn, &cs);
+    sincos(__ddiv_rn(dmul(two_pi, (double)i), (double)sp.Lm), &sn, &cs);
     twm[i] = make_float2((float)cs, (float)-sn);
   }
   if (i < sp.N) g[i] = sp.g[i];
@@ -101,50 +89,22 @@ extern "C" int frbx_fit_segments_noalloc(const frbx_setup *s, const void *vis_de
       (n_seg > 0 && (!segs || !out_dev)))
     return FRBX_EINVAL;
   if (((uintptr_t)vis_dev & 7u) != 0 || ((uintptr_t)out_dev & 7u) != 0) return FRBX_EINVAL;
-  const int N = s->n_chan, J = s->n_point;
-  if (N < 1 || N > kMaxChan || J < 2 || J > kMaxPoint || !(s->f_bw_mhz > 0) || !(s->t_ap_ms > 0) ||
-      !std::isfinite(s->f_bw_mhz) || !std::isfinite(s->t_ap_ms))
-    return FRBX_EINVAL;
   for (int d = 0; d < n_dm; ++d)
     if (!(dm[d] >= 0) || !std::isfinite(dm[d])) return FRBX_EINVAL;
-  // setup scalars on the host (stack only): f_ref, MBD grid, grid sizes
+  // setup scalars on the host (stack only), by the code frbx_create uses
+  SetupGrid sg;
+  const int rc = setup_grid(s, &sg);
+  if (rc != FRBX_OK) return rc;
+  const int N = sg.N, J = sg.J;
   SetupParams sp{};
   sp.N = N;
   sp.J = J;
-  sp.C = N * J;
+  sp.C = sg.C;
+  sp.Ls = sg.Ls;
+  sp.Lm = sg.Lm;
   sp.f_bw = s->f_bw_mhz;
-  double fmax = 0, fmin0 = s->f0_mhz[0];
-  for (int n = 0; n < N; ++n) {
-    if (!(s->f0_mhz[n] > 0) || !std::isfinite(s->f0_mhz[n])) return FRBX_EINVAL;
-    fmin0 = std::min(fmin0, s->f0_mhz[n]);
-    for (int j = 0; j < J; ++j) fmax = std::max(fmax, s->f0_mhz[n] + ((double)j * s->f_bw_mhz) / (double)J);
-  }
-  sp.f_ref = s->f_ref_dm_mhz != 0.0 ? s->f_ref_dm_mhz : fmax;
-  if (!(sp.f_ref >= fmax)) return FRBX_EINVAL;
-  long long off_khz[kMaxChan], gcd = 0;
-  for (int n = 0; n < N; ++n) {
-    const double o = (s->f0_mhz[n] - fmin0) * 1000.0, r = std::nearbyint(o);
-    if (std::fabs(o - r) > 1e-3) return FRBX_EINVAL;
-    off_khz[n] = (long long)r;
-    if (r != 0) gcd = std::gcd(gcd, (long long)r);
-  }
-  if (gcd == 0) gcd = (long long)std::nearbyint(s->f_bw_mhz * 1000.0);
-  if (gcd <= 0) return FRBX_EINVAL;
-  int gmax = 0;
-  for (int n = 0; n < N; ++n) {
-    if (off_khz[n] / gcd > kMaxLm) return FRBX_EUNSUPPORTED;
-    sp.g[n] = (int)(off_khz[n] / gcd);
-    gmax = std::max(gmax, sp.g[n]);
-  }
-  const int spad = s->sbd_pad ? s->sbd_pad : 2, mpad = s->mbd_pad ? s->mbd_pad : 2;
-  if (spad < 1 || mpad < 1) return FRBX_EINVAL;
-  int p2 = 1;
-  while (p2 < gmax + 1) p2 *= 2;
-  sp.Ls = spad * J;
-  sp.Lm = mpad * p2;
-  if ((sp.Ls & (sp.Ls - 1)) || (sp.Lm & (sp.Lm - 1)) || sp.Ls > kMaxLs || sp.Lm > kMaxLm ||
-      (long long)sp.Ls * sp.Lm > (1LL << 20))
-    return FRBX_EUNSUPPORTED;
+  sp.f_ref = sg.f_ref;
+  for (int n = 0; n < N; ++n) sp.g[n] = sg.g[n];
   // scratch layout, checked against the fixed size
   const int C = sp.C;
   size_t off = 0;

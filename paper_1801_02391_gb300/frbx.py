@@ -95,6 +95,11 @@ class frbx_batch_stats(ctypes.Structure):
                 ("time_tile", c_i32 * 16), ("reserved", c_i32), ("fit_ms", c_f64), ("launches", c_i64)]
 
 
+class frbx_limits(ctypes.Structure):
+    _fields_ = [("tree_chunk_bytes", c_i64), ("wait_cycles", c_i64), ("scratch_cap_bytes", c_i64),
+                ("hold_producers", c_i32), ("reserved", c_i32)]
+
+
 assert ctypes.sizeof(frbx_cand) == CAND_DTYPE.itemsize == 80
 assert ctypes.sizeof(frbx_event) == EVENT_DTYPE.itemsize == 28
 
@@ -125,6 +130,9 @@ SIGNATURES = {
     "frbx_batch_info": (c_i32, [c_vp, P(frbx_batch_stats)]),
     "frbx_search_batch": (c_i32, [c_vp, P(frbx_scan), c_i32, P(c_f64), c_i32, P(c_i32), c_i32, P(frbx_params),
                                   P(frbx_results), c_vp]),
+    "frbx_set_limits": (c_i32, [c_vp, P(frbx_limits)]),
+    "frbx_get_limits": (c_i32, [c_vp, P(frbx_limits)]),
+    "frbx_scratch_bytes": (c_i64, [c_vp]),
     "frbx_extract_events": (c_i32, [c_vp, c_i64, c_i32, c_i32, c_i32, P(c_i32), c_i32, c_i32, c_i32, c_i32,
                                     c_vp, c_i64, P(c_i64), c_vp, c_i64, P(c_i64), c_vp, c_i64, P(c_i64)]),
 }
@@ -311,6 +319,20 @@ class Handle:
 
     def launch_count(self) -> int:
         return int(load().frbx_last_launch_count(self.h))
+
+    def set_limits(self, tree_chunk_bytes=0, wait_cycles=0, scratch_cap_bytes=0, hold_producers=0):
+        """frbx_set_limits: zero in a field means its default (frbx_limits in include/frbx.h)."""
+        lim = frbx_limits(tree_chunk_bytes=int(tree_chunk_bytes), wait_cycles=int(wait_cycles),
+                          scratch_cap_bytes=int(scratch_cap_bytes), hold_producers=int(hold_producers))
+        _check(self.h, load().frbx_set_limits(self.h, ctypes.byref(lim)))
+
+    def get_limits(self) -> dict:
+        lim = frbx_limits()
+        _check(self.h, load().frbx_get_limits(self.h, ctypes.byref(lim)))
+        return {k: int(getattr(lim, k)) for k, _ in frbx_limits._fields_ if k != "reserved"}
+
+    def scratch_bytes(self) -> int:
+        return int(load().frbx_scratch_bytes(self.h))
 
     STAGES = ("shift_table", "fit", "normalise_baselines", "normalise_combos", "host_extract",
               "tree_sbd_kernels", "tree_mbd_kernels", "tree_chunks", "tree_tensor")

@@ -42,7 +42,7 @@ def test_struct_layouts_match_header(frbx, tmp_path):
     structs = {"frbx_setup": frbx.frbx_setup, "frbx_params": frbx.frbx_params, "frbx_seg": frbx.frbx_seg,
                "frbx_event": frbx.frbx_event, "frbx_cand": frbx.frbx_cand, "frbx_group": frbx.frbx_group,
                "frbx_results": frbx.frbx_results, "frbx_scan": frbx.frbx_scan,
-               "frbx_batch_stats": frbx.frbx_batch_stats}
+               "frbx_batch_stats": frbx.frbx_batch_stats, "frbx_limits": frbx.frbx_limits}
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', 'int main(void){']
     for name, cls in structs.items():
         lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
@@ -97,6 +97,26 @@ def test_create_rejects_bad_setups_before_touching_the_gpu(frbx):
     assert lib.frbx_create(None, ctypes.byref(h)) == frbx.FRBX_EINVAL
     assert lib.frbx_last_error(None) == b"null handle"
     lib.frbx_destroy(None)
+
+
+def test_limits_entry_points_reject_null_and_negative_without_a_gpu(frbx):
+    lib = frbx.load()
+    lim = frbx.frbx_limits()
+    assert lib.frbx_set_limits(None, ctypes.byref(lim)) == frbx.FRBX_EINVAL
+    assert lib.frbx_get_limits(None, ctypes.byref(lim)) == frbx.FRBX_EINVAL
+    assert lib.frbx_scratch_bytes(None) == -1
+
+
+def test_peak_probe_library_exports_its_header(frbx):
+    from paper_1801_02391_gb300 import peaks
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "frbx_peaks.h")).read(), flags=re.S)
+    names = sorted(set(re.findall(r"\b(frbx_[a-z_]+)\s*\(", text)))
+    lib = peaks.load()
+    assert names == sorted(peaks.SIGNATURES)
+    for n in names:
+        assert hasattr(lib, n), n
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    assert lib.frbx_peak_probe(9, 1, ctypes.byref(tf), ctypes.byref(ms), None) == -1  # rejected before any CUDA call
 
 
 def test_fp64_host_code_built_without_contraction():
