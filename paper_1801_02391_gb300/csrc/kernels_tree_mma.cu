@@ -126,6 +126,12 @@ __device__ __forceinline__ void tm_st(uint32_t taddr, const uint64_t (&v)[kQ / 2
                  : "memory");
   }
 }
+// three-input maximum of finite floats (IEEE, subnormals kept)
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+  float d;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+  return d;
+}
 __device__ __forceinline__ void tm_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
@@ -231,59 +237,69 @@ __global__ void __launch_bounds__((kEpi + 2) * 32, 1) k_tree_mma(const __grid_co
     }
     __syncwarp();
   } else if (warp == kMmaWarp) {
-    // ================= MMA issuer (one lane: its waits need no warp vote) =================
-    if (lane == 0) {
-      const uint32_t id64 = idesc_bf16(kTmCols), id128 = idesc_bf16(2 * kTmCols);
-      const int kk_steps = t.KA * 4;  // K = 16 per instruction, 4 per 64-wide atom
-      // descriptors of the K steps differ only in the start address field (address / 16, in
-      // the low 14 bits, which shared-memory offsets below 256 KB never carry out of)
-      const uint32_t a_half16 = (uint32_t)(t.KA * tc::kAtomBytes) >> 4;
-      const uint64_t w0 = tc::desc_sw128(tc::su32(sW));
-      const uint64_t sa0 = tc::desc_sw128(tc::su32(sA));
-      const uint32_t tile16 = (uint32_t)t.tile_bytes >> 4;
-      bool ok = true;
-      for (int i = 0, b = 0, ph = 0, slot = 0, sph = 0; i < n_ap; ++i) {
-        if (!tc::mbar_wait(&bar_afull[b], (uint32_t)ph, abortp, t.timeout) ||
-            !tc::mbar_wait(&bar_accempty[slot], (uint32_t)sph ^ 1u, abortp, t.timeout)) {
-          ok = false;
-          break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint64_t a0 = sa0 + (uint64_t)(b * tile16);
-        const uint32_t d_tmem = tmem + (uint32_t)(slot * kTmSlotCols);
+    // ================= MMA issuer =================
+    // The whole warp runs the loop, so its descriptor arithmetic stays warp-uniform (no
+    // per-instruction moves into uniform registers); one elected lane issues the MMAs and
+    // commits, which keeps the issue rate at the tensor pipe's pace.
+    const bool leader = tc::elect_one();
+    const uint32_t id64 = idesc_bf16(kTmCols), id128 = idesc_bf16(2 * kTmCols);
+    // descriptors of the K steps differ only in the start address field (address / 16, in
+    // the low 14 bits, which shared-memory offsets below 256 KB never carry out of)
+    const uint32_t a_half16 = (uint32_t)(t.KA * tc::kAtomBytes) >> 4;
+    const uint64_t w0 = tc::desc_sw128(tc::su32(sW));
+    const uint64_t sa0 = tc::desc_sw128(tc::su32(sA));
+    const uint32_t tile16 = (uint32_t)t.tile_bytes >> 4;
+    bool ok = true;
+    for (int i = 0, b = 0, ph = 0, slot = 0, sph = 0; i < n_ap; ++i) {
+      const bool got = tc::mbar_wait(&bar_afull[b], (uint32_t)ph, abortp, t.timeout) &&
+                       tc::mbar_wait(&bar_accempty[slot], (uint32_t)sph ^ 1u, abortp, t.timeout);
+      if (!__all_sync(0xffffffffu, got)) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint64_t a0 = sa0 + (uint64_t)(b * tile16);
+      const uint32_t d_tmem = tmem + (uint32_t)(slot * kTmSlotCols);
+      if (leader) {
         // D[0:64] = A_hi W_hi, D[64:128] = A_hi W_lo (one N = 128 MMA per K step) + A_lo W_hi
-#pragma unroll 4
-        for (int kk = 0; kk < kk_steps; ++kk) {
-          const uint32_t ao = (uint32_t)(((kk >> 2) * tc::kAtomBytes + (kk & 3) * 32) >> 4);
-          const uint32_t bo = (uint32_t)(((kk >> 2) * 2 * kTmWAtom + (kk & 3) * 32) >> 4);
-          mma_bf16(d_tmem, a0 + ao, w0 + bo, id128, kk > 0 ? 1u : 0u);
+        for (int ka = 0; ka < t.KA; ++ka) {
+#pragma unroll
+          for (int k4 = 0; k4 < 4; ++k4) {
+            const uint32_t ao = (uint32_t)((ka * tc::kAtomBytes + k4 * 32) >> 4);
+            const uint32_t bo = (uint32_t)((ka * 2 * kTmWAtom + k4 * 32) >> 4);
+            mma_bf16(d_tmem, a0 + ao, w0 + bo, id128, (ka | k4) ? 1u : 0u);
+          }
         }
-#pragma unroll 4
-        for (int kk = 0; kk < kk_steps; ++kk) {
-          const uint32_t ao = (uint32_t)(((kk >> 2) * tc::kAtomBytes + (kk & 3) * 32) >> 4);
-          const uint32_t bo = (uint32_t)(((kk >> 2) * 2 * kTmWAtom + (kk & 3) * 32) >> 4);
-          mma_bf16(d_tmem + (uint32_t)kTmCols, a0 + a_half16 + ao, w0 + bo, id64, 1u);
+        for (int ka = 0; ka < t.KA; ++ka) {
+#pragma unroll
+          for (int k4 = 0; k4 < 4; ++k4) {
+            const uint32_t ao = (uint32_t)((ka * tc::kAtomBytes + k4 * 32) >> 4);
+            const uint32_t bo = (uint32_t)((ka * 2 * kTmWAtom + k4 * 32) >> 4);
+            mma_bf16(d_tmem + (uint32_t)kTmCols, a0 + a_half16 + ao, w0 + bo, id64, 1u);
+          }
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                      ::"r"(tc::su32(&bar_accfull[slot])) : "memory");
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                      ::"r"(tc::su32(&bar_aempty[b])) : "memory");
-        if (++b == nbuf) {
-          b = 0;
-          ph ^= 1;
-        }
-        if (++slot == kSlots) {
-          slot = 0;
-          sph ^= 1;
-        }
       }
-      if (!ok) *abortp = 1;
-      // drain: a last commit lands only when every MMA this thread issued has completed
+      __syncwarp();
+      if (++b == nbuf) {
+        b = 0;
+        ph ^= 1;
+      }
+      if (++slot == kSlots) {
+        slot = 0;
+        sph ^= 1;
+      }
+    }
+    if (!ok && leader) *abortp = 1;
+    // drain: a last commit lands only when every MMA the leader issued has completed
+    if (leader)
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                    ::"r"(tc::su32(&bar_drain)) : "memory");
-      if (!tc::mbar_wait(&bar_drain, 0, nullptr, t.drain_timeout)) *abortp = 1;
-    }
     __syncwarp();
+    if (!__all_sync(0xffffffffu, tc::mbar_wait(&bar_drain, 0, nullptr, t.drain_timeout)) && leader) *abortp = 1;
   } else {
     // ================= epilogue: window tree and maxima =================
     const int quarter = warp & 3, part = warp >> 2;
@@ -296,14 +312,14 @@ __global__ void __launch_bounds__((kEpi + 2) * 32, 1) k_tree_mma(const __grid_co
     int woff[kTmMaxLev + 1];  // first slot of the window emitted at each level (-1: none)
 #pragma unroll
     for (int e = 0; e <= kTmMaxLev; ++e) woff[e] = t.emit_w[e] >= 0 ? t.win_off[t.emit_w[e]] : -1;
-    uint64_t pre[kP], pim[kP];  // G_1(k - 1), carried in registers from the previous AP
+    uint64_t ga_re[kP], ga_im[kP], gb_re[kP], gb_im[kP];  // G_1 of two consecutive APs, alternating
 #pragma unroll
-    for (int p = 0; p < kP; ++p) pre[p] = pim[p] = 0ull;
+    for (int p = 0; p < kP; ++p) ga_re[p] = ga_im[p] = gb_re[p] = gb_im[p] = 0ull;
     for (int a = 0; a + 2 <= t.nlev; ++a) {
       if (a < n_tanc) {
         const uint32_t ab = lane_base + (uint32_t)(kAnc + a * kTmCols);
-        tm_st<kQ>(ab + c_re, pre);
-        tm_st<kQ>(ab + c_im, pim);
+        tm_st<kQ>(ab + c_re, ga_re);
+        tm_st<kQ>(ab + c_im, ga_im);
       } else {
         ulonglong2 *q = my_anc + (size_t)(a - n_tanc) * 16 * tc::kRows;
 #pragma unroll
@@ -314,120 +330,125 @@ __global__ void __launch_bounds__((kEpi + 2) * 32, 1) k_tree_mma(const __grid_co
       }
     }
     tm_wait_st();
-    bool ok = true;
-    for (int i = 0, slot = 0, sph = 0; i < n_ap; ++i) {
-      const int k = kb + i;
-      if (!__all_sync(0xffffffffu, tc::mbar_wait(&bar_accfull[slot], (uint32_t)sph, abortp, t.timeout))) {
-        ok = false;  // uniform within the warp: tcgen05.ld is warp-collective
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int E = t.nlev == 0 ? 0 : min(t.nlev, __ffs(k + 1));  // levels whose window ends at k
-      uint64_t cre[kP], cim[kP];
-      {
-        uint64_t lre[kP], lim[kP];
-        const uint32_t cur = lane_base + (uint32_t)(slot * kTmSlotCols);
-        tm_ld<kQ>(cur + c_re, cre);
-        tm_ld<kQ>(cur + c_im, cim);
-        tm_ld<kQ>(cur + kTmCols + c_re, lre);
-        tm_ld<kQ>(cur + kTmCols + c_im, lim);
-        tm_wait_ld();
+    // Maximum of one emitted segment's cells: packed keys (|G|^2 with the 6 low mantissa bits
+    // replaced by 31 - j, so the lower q wins a tie), a three-input maximum tree (the keys are
+    // non-negative floats, ordered as their bit patterns), the warp maximum, and one 64-bit
+    // atomicMax into the series by the lane holding it (tied lanes share j; the atomicMax keeps
+    // the lowest of their indices).
+    auto emit = [&](const int e, const int k0, const uint64_t(&gre)[kP], const uint64_t(&gim)[kP]) {
+      float kf[kQ];
 #pragma unroll
-        for (int p = 0; p < kP; ++p) {
-          cre[p] = add2(cre[p], lre[p]);
-          cim[p] = add2(cim[p], lim[p]);
-        }
+      for (int p = 0; p < kP; ++p) {
+        uint32_t lo, hi;
+        upk(fma2(gre[p], gre[p], mul2(gim[p], gim[p])), lo, hi);
+        kf[2 * p] = __uint_as_float((lo & ~63u) | (unsigned)(31 - 2 * p));
+        kf[2 * p + 1] = __uint_as_float((hi & ~63u) | (unsigned)(30 - 2 * p));
+      }
+      float top;
+      if constexpr (kQ == 16) {
+        float m5[5];
+#pragma unroll
+        for (int j = 0; j < 5; ++j) m5[j] = fmax3(kf[3 * j], kf[3 * j + 1], kf[3 * j + 2]);
+        top = fmax3(fmax3(m5[0], m5[1], m5[2]), fmax3(m5[3], m5[4], kf[15]), 0.f);
+      } else {
+        static_assert(kQ == 8, "8 or 16 cells per thread");
+        top = fmax3(fmax3(kf[0], kf[1], kf[2]), fmax3(kf[3], kf[4], kf[5]), fmaxf(kf[6], kf[7]));
+      }
+      const unsigned tkey = __float_as_uint(top);
+      const unsigned wmax = __reduce_max_sync(0xffffffffu, tkey);
+      if (tkey == wmax) {
+        const unsigned idx = idx0 + (unsigned)lane * (unsigned)t.Lm + (31u - (wmax & 63u));
+        // slot of the segment: windows of 2^e APs start every 2^(e-1) APs (every AP for e = 0)
+        atomicMax(keys + woff[e] + (k0 >> (e > 0 ? e - 1 : 0)),
+                  ((unsigned long long)(wmax & ~63u) << 32) | (unsigned long long)(~idx));
+      }
+    };
+    // One AP: cur receives G_1(k); prev holds G_1(k - 1).  Returns false when a wait gave up.
+    auto one_ap = [&](const int i, const int slot, const uint32_t sph, const uint64_t(&pre)[kP],
+                      const uint64_t(&pim)[kP], uint64_t(&cre)[kP], uint64_t(&cim)[kP]) -> bool {
+      const int k = kb + i;
+      if (!__all_sync(0xffffffffu, tc::mbar_wait(&bar_accfull[slot], sph, abortp, t.timeout))) return false;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      uint64_t lre[kP], lim[kP];
+      const uint32_t cur = lane_base + (uint32_t)(slot * kTmSlotCols);
+      tm_ld<kQ>(cur + c_re, cre);
+      tm_ld<kQ>(cur + c_im, cim);
+      tm_ld<kQ>(cur + kTmCols + c_re, lre);
+      tm_ld<kQ>(cur + kTmCols + c_im, lim);
+      // levels whose window ends at k, and which of them emit a segment of this time tile
+      // (uniform across the CTA)
+      const int E = t.nlev == 0 ? 0 : min(t.nlev, __ffs(k + 1));
+      unsigned em = 0;
+#pragma unroll
+      for (int e = 0; e <= kTmMaxLev; ++e) {
+        const int k0 = k - (1 << e) + 1;
+        if (e <= E && woff[e] >= 0 && k0 >= kb && k0 < kb + t.TT) em |= 1u << e;
+      }
+      tm_wait_ld();
+#pragma unroll
+      for (int p = 0; p < kP; ++p) {
+        cre[p] = add2(cre[p], lre[p]);
+        cim[p] = add2(cim[p], lim[p]);
       }
       // G_1(k) is in the warp's registers: its slot may take AP k + kSlots.  One arrival per
       // warp: 256 arrivals on one mbarrier serialise as shared-memory atomics.
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&bar_accempty[slot]);
-      if (++slot == kSlots) {
-        slot = 0;
-        sph ^= 1;
-      }
+      if (em & 1u) emit(0, k, cre, cim);
+      if (E == 0) return true;
       uint64_t are[kP], aim[kP];
 #pragma unroll
-      for (int e = 0; e <= kTmMaxLev; ++e) {
-        if (e > E) break;
-        if (e == 0) {
-#pragma unroll
-          for (int p = 0; p < kP; ++p) {
-            are[p] = cre[p];
-            aim[p] = cim[p];
-          }
-        } else if (e == 1) {
-#pragma unroll
-          for (int p = 0; p < kP; ++p) {
-            are[p] = add2(pre[p], cre[p]);
-            aim[p] = add2(pim[p], cim[p]);
-          }
-        } else {
-          // anchor of level e - 1: the previous window-2^(e-1) matrix, first half of this one
-          uint64_t ore[kP], oim[kP];
-          const bool in_tmem = e - 2 < n_tanc;  // uniform
-          if (in_tmem) {
-            const uint32_t ab = lane_base + (uint32_t)(kAnc + (e - 2) * kTmCols);
-            tm_ld<kQ>(ab + c_re, ore);
-            tm_ld<kQ>(ab + c_im, oim);
-            tm_wait_ld();
-            tm_st<kQ>(ab + c_re, are);
-            tm_st<kQ>(ab + c_im, aim);
-          } else {
-            ulonglong2 *q = my_anc + (size_t)(e - 2 - n_tanc) * 16 * tc::kRows;
-#pragma unroll
-            for (int u = 0; u < kQ / 4; ++u) {
-              const ulonglong2 r = q[u * tc::kRows], m = q[(8 + u) * tc::kRows];
-              ore[2 * u] = r.x;
-              ore[2 * u + 1] = r.y;
-              oim[2 * u] = m.x;
-              oim[2 * u + 1] = m.y;
-              q[u * tc::kRows] = make_ulonglong2(are[2 * u], are[2 * u + 1]);
-              q[(8 + u) * tc::kRows] = make_ulonglong2(aim[2 * u], aim[2 * u + 1]);
-            }
-          }
-#pragma unroll
-          for (int p = 0; p < kP; ++p) {
-            are[p] = add2(are[p], ore[p]);
-            aim[p] = add2(aim[p], oim[p]);
-          }
-          if (in_tmem) tm_wait_st();
-        }
-        const int k0 = k - (1 << e) + 1;
-        if (woff[e] >= 0 && k0 >= kb && k0 < kb + t.TT) {  // uniform across the CTA
-          // packed key: |G|^2 with its 6 low mantissa bits replaced by 31 - j (lower q wins a tie)
-          unsigned kk[kQ];
-#pragma unroll
-          for (int p = 0; p < kP; ++p) {
-            uint32_t lo, hi;
-            upk(fma2(are[p], are[p], mul2(aim[p], aim[p])), lo, hi);
-            kk[2 * p] = (lo & ~63u) | (unsigned)(31 - 2 * p);
-            kk[2 * p + 1] = (hi & ~63u) | (unsigned)(30 - 2 * p);
-          }
-#pragma unroll
-          for (int wdt = kQ / 2; wdt >= 1; wdt >>= 1) {
-#pragma unroll
-            for (int j = 0; j < wdt; ++j) kk[j] = max(kk[j], kk[j + wdt]);
-          }
-          // the lane holding the warp maximum merges it; tied lanes share j, and the atomicMax
-          // keeps the lowest of their indices, the lowest lane
-          const unsigned wmax = __reduce_max_sync(0xffffffffu, kk[0]);
-          if (kk[0] == wmax) {
-            const unsigned j = 31u - (wmax & 63u);
-            const unsigned idx = idx0 + (unsigned)lane * (unsigned)t.Lm + j;
-            // slot of the segment: windows of 2^e APs start every 2^(e-1) APs (every AP for e = 0)
-            atomicMax(keys + woff[e] + (k0 >> (e > 0 ? e - 1 : 0)),
-                      ((unsigned long long)(wmax & ~63u) << 32) | (unsigned long long)(~idx));
-          }
-        }
-      }
-#pragma unroll
       for (int p = 0; p < kP; ++p) {
-        pre[p] = cre[p];
-        pim[p] = cim[p];
+        are[p] = add2(pre[p], cre[p]);
+        aim[p] = add2(pim[p], cim[p]);
+      }
+      if (em & 2u) emit(1, k - 1, are, aim);
+#pragma unroll
+      for (int e = 2; e <= kTmMaxLev; ++e) {
+        if (e > E) break;
+        uint64_t ore[kP], oim[kP];
+        const bool in_tmem = e - 2 < n_tanc;  // uniform
+        if (in_tmem) {
+          const uint32_t ab = lane_base + (uint32_t)(kAnc + (e - 2) * kTmCols);
+          tm_ld<kQ>(ab + c_re, ore);
+          tm_ld<kQ>(ab + c_im, oim);
+          tm_wait_ld();
+          tm_st<kQ>(ab + c_re, are);
+          tm_st<kQ>(ab + c_im, aim);
+        } else {
+          ulonglong2 *q = my_anc + (size_t)(e - 2 - n_tanc) * 16 * tc::kRows;
+#pragma unroll
+          for (int u = 0; u < kQ / 4; ++u) {
+            const ulonglong2 r = q[u * tc::kRows], m = q[(8 + u) * tc::kRows];
+            ore[2 * u] = r.x;
+            ore[2 * u + 1] = r.y;
+            oim[2 * u] = m.x;
+            oim[2 * u + 1] = m.y;
+            q[u * tc::kRows] = make_ulonglong2(are[2 * u], are[2 * u + 1]);
+            q[(8 + u) * tc::kRows] = make_ulonglong2(aim[2 * u], aim[2 * u + 1]);
+          }
+        }
+#pragma unroll
+        for (int p = 0; p < kP; ++p) {
+          are[p] = add2(are[p], ore[p]);
+          aim[p] = add2(aim[p], oim[p]);
+        }
+        if (in_tmem) tm_wait_st();
+        if ((em >> e) & 1u) emit(e, k - (1 << e) + 1, are, aim);
+      }
+      return true;
+    };
+    bool ok = true;
+    int i = 0;
+    uint32_t sph = 0;
+    for (; i + 1 < n_ap; i += 2, sph ^= 1u) {
+      if (!one_ap(i, 0, sph, gb_re, gb_im, ga_re, ga_im) || !one_ap(i + 1, 1, sph, ga_re, ga_im, gb_re, gb_im)) {
+        ok = false;
+        break;
       }
     }
+    if (ok && i < n_ap && !one_ap(i, 0, sph, gb_re, gb_im, ga_re, ga_im)) ok = false;
     if (!ok) *abortp = 1;
   }
 

@@ -20,15 +20,22 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *b) {
   asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(su32(b)) : "memory");
 }
 // Bounded wait for the completion of the phase with the given parity.  Returns false on
-// timeout or when another role raised the abort flag (abort_flag may be null).
+// timeout or when another role raised the abort flag (abort_flag may be null).  After a first
+// probe, each try_wait may suspend the warp for up to kWaitSuspendNs (it wakes when the phase
+// completes), so a waiting role takes no issue slots from the others; the limit and the abort
+// flag are checked between probes.
+constexpr uint32_t kWaitSuspendNs = 20000;
 __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, volatile int *abort_flag,
                                           long long limit) {
-  const long long t0 = clock64();
   const uint32_t addr = su32(b);
+  uint32_t ok;
+  asm volatile("{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.b32 %0, 1, 0, P;\n}\n"
+               : "=r"(ok) : "r"(addr), "r"(parity) : "memory");
+  if (ok) return true;
+  const long long t0 = clock64();
   for (;;) {
-    uint32_t ok;
-    asm volatile("{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.b32 %0, 1, 0, P;\n}\n"
-                 : "=r"(ok) : "r"(addr), "r"(parity) : "memory");
+    asm volatile("{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2, %3;\n selp.b32 %0, 1, 0, P;\n}\n"
+                 : "=r"(ok) : "r"(addr), "r"(parity), "r"(kWaitSuspendNs) : "memory");
     if (ok) return true;
     if (abort_flag && *abort_flag) return false;
     if (clock64() - t0 > limit) return false;
@@ -50,6 +57,14 @@ __device__ __forceinline__ uint32_t a_offset(int row, int k) {
 __device__ __forceinline__ uint32_t a_offset8(int row, int k) {
   return (uint32_t)((k >> 7) * kAtomBytes + (row >> 3) * 1024 + (row & 7) * 128 +
                     ((((k & 127) >> 4) ^ (row & 7)) << 4) + (k & 15));
+}
+
+// true in exactly one lane of the (fully active) warp
+__device__ __forceinline__ bool elect_one() {
+  uint32_t p;
+  asm volatile("{\n .reg .b32 rx;\n .reg .pred px;\n elect.sync rx|px, %1;\n selp.u32 %0, 1, 0, px;\n}\n"
+               : "=r"(p) : "r"(0xffffffffu));
+  return p != 0;
 }
 
 __device__ __forceinline__ void named_sync(int id, int n) {
