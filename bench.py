@@ -86,6 +86,7 @@ def parse():
     ap.add_argument("--batch-bl", type=int, default=3, help="baselines per scan of the batched variant")
     ap.add_argument("--batch-scale", type=float, default=0.25, help="scan-length factor of the batched variant")
     ap.add_argument("--batch-steps", type=int, default=2)
+    ap.add_argument("--variant-steps", type=int, default=2, help="timed steps of each variant")
     return ap.parse_args()
 
 
@@ -165,11 +166,6 @@ def n_segments(wl, dk_max):
             if r >= 0:
                 tot += r // max(1, l // 2) + 1
     return tot * wl.n_bl
-
-
-def gemm_flops_per_segment(N, Ls, Lm):
-    """Dense DFT-GEMM form of the MBD transform: Ls rows x 2N real inputs x 2Lm real outputs."""
-    return 2.0 * Ls * (2 * N) * (2 * Lm)
 
 
 def fft_flops_per_segment(N, Ls, Lm):
@@ -453,43 +449,102 @@ def main():
             "gpu_launches": launches, "roofline": roof, "clocks": clocks, "peaks_measured": own,
             "stages_ms": stages, "segments_per_step": n_seg,
             "pulses": int(out["counts"]["pulses"]), "groups": int(out["counts"]["groups"])}
-    # the tensor-core forms (MBD transform as a BF16 / FP8 DFT-GEMM on tcgen05), same workload
+    # variants on this GPU, each timed with CUDA events on the stream after one untimed call:
+    #  * the window tree's lower-precision forms on the same workload (kernel 7: one BF16 product
+    #    per AP, kernel 8: E4M3), pulses compared with the default path's;
+    #  * the windowed regime: the same workload with a +-64 ns SBD search window (9 of 128 SBD
+    #    rows) and the whole MBD range, where the metric's 8 B/cell HBM fraction applies;
+    #  * config 1 (the small S-band cube, plain) and config 4 (the same cube with the MBD
+    #    transform as a BF16 / E4M3 DFT-GEMM per segment, kernels 3 and 5).
     line_variants = {}
-    if not args.no_variants and args.kernel == 0 and h.Ls in (64, 128):
-        for vname, vk, vdt in (("tensor_bf16", 3, "bf16 operands, f32 accumulate (MBD DFT-GEMM); f32 elsewhere"),
-                               ("tensor_fp8", 5, "fp8 e4m3 operands (A scaled per segment), f32 accumulate "
-                                                 "(MBD DFT-GEMM); f32 elsewhere")):
+
+    def timed(hh, vis, wll, cmb, kernel, steps, **kw):
+        hh.search(vis, wll.dms, wll.windows, combos=cmb, kernel=kernel, stream=stream, **kw)
+        barrier()
+        v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fits, mbds, o = [], [], None
+        v0.record(stream)
+        for _ in range(steps):
+            o = hh.search(vis, wll.dms, wll.windows, combos=cmb, kernel=kernel, stream=stream, **kw)
+            stg = hh.stage_times()
+            fits.append(stg["fit"])
+            mbds.append(stg["tree_mbd_kernels"])
+        v1.record(stream)
+        torch.cuda.synchronize()
+        vms = max_over_ranks(v0.elapsed_time(v1) / steps)
+        return vms, statistics.mean(fits), statistics.mean(mbds), o
+
+    if not args.no_variants and args.kernel == 0 and args.workload == "vgos":
+        for vname, vk, vdt, peak, pkind in (
+                ("tree_bf16", 7, "bf16 operands (one product per AP), f32 accumulate (MBD transform on tcgen05); "
+                                 "f32 elsewhere", peaks["bf16_tflops_sustained"], peaks_kind + " sustained bf16"),
+                ("tree_fp8", 8, "e4m3 operands (A scaled per AP by a power of two), f32 accumulate (MBD transform "
+                                "on tcgen05); f32 elsewhere", own["fp8_mma_sustained"],
+                 "this GPU's sustained E4M3 tcgen05 rate (libfrbx_peaks)")):
             try:
-                h.search(vis_dev, wl.dms, wl.windows, combos=combos, kernel=vk, stream=stream)
-                barrier()
-                v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                vsteps = 1
-                vfit = []
-                v0.record(stream)
-                for _ in range(vsteps):
-                    o3 = h.search(vis_dev, wl.dms, wl.windows, combos=combos, kernel=vk, stream=stream)
-                    vfit.append(h.stage_times()["fit"])
-                v1.record(stream)
-                torch.cuda.synchronize()
-                vms = max_over_ranks(v0.elapsed_time(v1) / vsteps)
-                gflops = n_seg * gemm_flops_per_segment(wl.n_chan, h.Ls, h.Lm)
-                vach = gflops / (statistics.mean(vfit) / 1e3) / 1e12
-                # sustained dense MMA rate of the operands' own type: BF16 from MEASURED_PEAKS.json,
-                # E4M3 from this GPU's own probe (libfrbx_peaks)
-                vpeak = own["fp8_mma_sustained"] if vk == 5 else peaks["bf16_tflops_sustained"]
+                vms, vfit, vmbd, o3 = timed(h, vis_dev, wl, combos, vk, args.variant_steps)
+                n_ap = wl.n_bl * sum(max(0, wl.T - int(x)) for x in dk_max)
+                kdim = 64 * ((2 * wl.n_chan + 63) // 64) if vk == 7 else 32 * ((2 * wl.n_chan + 31) // 32)
+                gemm = n_ap * 2.0 * h.Ls * kdim * 2 * h.Lm
                 line_variants[vname] = {
-                    "value": world * cells / (vms / 1e3), "unit": "cells/s", "ms_per_step": vms, "steps": vsteps,
-                    "dtype": vdt,
-                    "roofline": {"bound": "tensor", "kernel": "k_fit_mma", "achieved": vach, "peak": vpeak,
-                                 "unit": "TFLOP/s", "frac": vach / vpeak, "traffic": None,
-                                 "peak_kind": ("this GPU's sustained E4M3 tcgen05 rate (libfrbx_peaks)" if vk == 5
-                                               else peaks_kind + " sustained bf16"),
-                                 "work": f"{n_seg} segments x {gemm_flops_per_segment(wl.n_chan, h.Ls, h.Lm):.0f} flop "
-                                         "(dense DFT-GEMM of the MBD transform)",
-                                 "fit_ms": statistics.mean(vfit)},
-                    "pulses": int(o3["counts"]["pulses"]), "groups": int(o3["counts"]["groups"])}
+                    "value": world * cells / (vms / 1e3), "unit": "cells/s", "ms_per_step": vms,
+                    "steps": args.variant_steps, "dtype": vdt,
+                    "roofline": {"bound": "tensor", "kernel": "k_tree_mma", "achieved": flops / (vmbd / 1e3) / 1e12,
+                                 "peak": peak, "unit": "TFLOP/s", "frac": flops / (vmbd / 1e3) / 1e12 / peak,
+                                 "traffic": None, "peak_kind": pkind, "work": roof["work"],
+                                 "executed_tensor": {"achieved": gemm / (vmbd / 1e3) / 1e12,
+                                                     "frac": gemm / (vmbd / 1e3) / 1e12 / peak,
+                                                     "work": f"{n_ap} APs x one GEMM of Ls x 2N x 2Lm"},
+                                 "kernel_ms": vmbd, "fit_ms": vfit},
+                    "pulses": int(o3["counts"]["pulses"]), "pulses_default_path": int(out["counts"]["pulses"]),
+                    "groups": int(o3["counts"]["groups"])}
             except Exception as exc:  # a variant that cannot run on this setup is reported, not fatal
                 line_variants[vname] = {"unavailable": str(exc)}
+        try:
+            sbd_win = (-64.0, 64.0)
+            vms, vfit, vmbd, o4 = timed(h, vis_dev, wl, combos, 0, args.variant_steps, sbd_win_ns=sbd_win)
+            sbd_ax = (np.where(np.arange(h.Ls) < h.Ls // 2, np.arange(h.Ls), np.arange(h.Ls) - h.Ls) * wl.n_point
+                      * 1000.0) / (h.Ls * wl.f_bw_mhz)
+            rows = int(np.sum((sbd_ax >= sbd_win[0]) & (sbd_ax <= sbd_win[1])))
+            wcells = cells  # the metric's cells count the search volume as it is defined (bl x DM x AP x point)
+            hbm_w = 8.0 * wcells / (vms / 1e3) / (peaks["hbm_gbs"] * 1e9)
+            line_variants["windowed"] = {
+                "value": world * wcells / (vms / 1e3), "unit": "cells/s", "ms_per_step": vms,
+                "steps": args.variant_steps, "dtype": dtype,
+                "sbd_window_ns": list(sbd_win), "sbd_rows_searched": rows, "mbd": "whole grid",
+                "roofline": {"bound": "hbm", "kernel": "search (8 B per cell)", "achieved": 8.0 * wcells / (vms / 1e3) / 1e9,
+                             "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": hbm_w, "traffic": None,
+                             "peak_kind": peaks_kind, "kernel_ms": vmbd, "fit_ms": vfit,
+                             "note": "the metric's HBM fraction: 8 B per (bl, DM, AP, point) cell over the step time"},
+                "pulses": int(o4["counts"]["pulses"])}
+        except Exception as exc:
+            line_variants["windowed"] = {"unavailable": str(exc)}
+    if not args.no_variants and args.kernel == 0 and args.workload == "vgos":
+        try:
+            ws, wcombos = make_workload("small")
+            svis = torch.from_numpy(synth.generate(ws)).cuda()
+            hs = frbx.Handle.from_workload(ws)
+            scells = cells_of(ws)
+            base = None
+            for vname, vk, vdt in (("config1_small", 0, "f32"),
+                                   ("config4_bf16", 3, "bf16 operands, f32 accumulate (MBD DFT-GEMM per segment)"),
+                                   ("config4_fp8", 5, "e4m3 operands (A scaled per segment), f32 accumulate "
+                                                      "(MBD DFT-GEMM per segment)")):
+                vms, vfit, _, o5 = timed(hs, svis, ws, wcombos, vk, max(3, args.variant_steps))
+                ent = {"value": world * scells / (vms / 1e3), "unit": "cells/s", "ms_per_step": vms, "fit_ms": vfit,
+                       "dtype": vdt, "workload": workload_config("small", ws)["workload"],
+                       "pulses": int(o5["counts"]["pulses"]), "groups": int(o5["counts"]["groups"])}
+                if base is None:
+                    base = o5
+                else:
+                    a = {(int(p["series"]), int(p["dm_idx"]), int(p["k0"]), int(p["width"])) for p in base["pulses"]}
+                    b2 = {(int(p["series"]), int(p["dm_idx"]), int(p["k0"]), int(p["width"])) for p in o5["pulses"]}
+                    ent["pulses_same_as_f32"] = len(a & b2)
+                    ent["pulses_f32"] = len(a)
+                line_variants[vname] = ent
+            del svis
+        except Exception as exc:
+            line_variants["config1_small"] = {"unavailable": str(exc)}
     if not args.no_variants and args.kernel == 0:
         try:
             line_variants["batch"] = run_batch_variant(frbx, torch, stream, args.batch_bl, args.batch_scale,

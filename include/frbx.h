@@ -98,8 +98,11 @@ typedef struct frbx_setup {
  *                5 = as 3 with FP8 E4M3 operands (about 6e-2 relative error);
  *                6 = window tree with the MBD transform as a three-term split-BF16
  *                    tensor-core GEMM, FP32 accumulation (about 1e-5 relative; Ls 128,
- *                    n_chan <= 64, whole grid).
- *                frbx_fit_segments treats 4 and 6 as 0 (a list has no window structure).
+ *                    n_chan <= 64, Lm a multiple of 32; delay windows allowed);
+ *                7 = as 6 with one BF16 product per AP (about 3e-3 relative);
+ *                8 = as 6 with E4M3 operands, A scaled per AP by a power of two (about 4e-2
+ *                    relative).
+ *                frbx_fit_segments treats 4, 6, 7 and 8 as 0 (a list has no window structure).
  */
 typedef struct frbx_params {
   float threshold;
@@ -449,12 +452,12 @@ int64_t frbx_last_launch_count(const frbx_handle *h);
 /*
  * Per-handle resource and robustness limits.  The paper has no counterpart; these control how
  * the library runs the method, never what it computes.  Zero in a field means its default.
- *  tree_chunk_bytes   window-tree fits (kernels 4 and 6; frbx_search): device bytes of one of the
+ *  tree_chunk_bytes   window-tree fits (kernels 4, 6, 7, 8; frbx_search): device bytes of one of the
  *                     two scratch sets that the chunked SBD / MBD passes alternate between.
  *                     Default: a quarter of the free device memory, at most 16 GiB.  A small value
  *                     gives more chunks and the same results.
  *  wait_cycles        limit, in SM clock cycles, of every pipeline wait inside the tensor-core
- *                     kernels (kernels 3, 5 and 6).  Default 2e9.  When a wait runs out the call
+ *                     kernels (kernels 3, 5, 6, 7 and 8).  Default 2e9.  When a wait runs out the call
  *                     returns FRBX_ETIMEOUT.  The waits that drain copies and MMAs still in
  *                     flight before a CTA exits keep the 2e9 limit, so no CTA leaves work behind.
  *  scratch_cap_bytes  cap on the device scratch the handle holds (the buffers it grows on demand;

@@ -365,6 +365,7 @@ int frbx_create(const frbx_setup *s, frbx_handle **out) {
   // q, then Im G) split as W = W_hi + W_lo in BF16, in 128-byte swizzled images; per 64-wide
   // K atom the 64 hi rows are followed by the 64 lo rows, so [W_hi; W_lo] is one 128-row operand
   std::vector<uint16_t> wtree;
+  std::vector<uint8_t> wtree8;
   if (frbx::tree_mma_supported(h->Ls, h->Lm, N, J)) {
     const int KA = (2 * N + 63) / 64, rows = 64, n_qb = h->Lm / 32, atom = rows * 128;
     const int wb = 2 * KA * atom;  // bytes per block: per K atom, hi rows then lo rows
@@ -403,6 +404,26 @@ int frbx_create(const frbx_setup *s, frbx_handle **out) {
         }
       }
     h->wtree_bytes = wb;
+    // the E4M3 form: per block of 32 q, the same 64 rows (Re G of the 32 q, then Im G) rounded
+    // once to E4M3, 128 K values per 128-byte row
+    const int KA8 = (2 * N + 127) / 128, wb8 = KA8 * rows * 128;
+    wtree8.assign((size_t)n_qb * wb8, 0);
+    auto put8 = [&](int qb, int R, int k, double v) {
+      const size_t off = (size_t)qb * wb8 + (size_t)(k / 128) * rows * 128 + (size_t)(R / 8) * 1024 +
+                         (size_t)(R % 8) * 128 + (size_t)((((k % 128) / 16) ^ (R % 8)) * 16) + (size_t)(k % 16);
+      wtree8[off] = to_e4m3(v);
+    };
+    for (int qb = 0; qb < n_qb; ++qb)
+      for (int R = 0; R < rows; ++R) {
+        const int q = qb * 32 + (R % 32);
+        const bool im = R >= 32;
+        for (int n = 0; n < N; ++n) {
+          const long long ex = ((long long)h->g[(size_t)n] * q) % h->Lm;
+          const double th = two_pi * (double)ex / (double)h->Lm;
+          put8(qb, R, n, im ? -std::sin(th) : std::cos(th));
+          put8(qb, R, N + n, im ? std::cos(th) : std::sin(th));
+        }
+      }
   }
   cudaError_t e = cudaGetDevice(&h->device);
   if (e == cudaSuccess) e = upload(&h->d_f, h->f);
@@ -419,6 +440,7 @@ int frbx_create(const frbx_setup *s, frbx_handle **out) {
   if (e == cudaSuccess && !bimg.empty()) e = upload((uint16_t **)&h->d_bimg, bimg);
   if (e == cudaSuccess && !bimg8.empty()) e = upload((uint8_t **)&h->d_bimg8, bimg8);
   if (e == cudaSuccess && !wtree.empty()) e = upload((uint16_t **)&h->d_wtree, wtree);
+  if (e == cudaSuccess && !wtree8.empty()) e = upload((uint8_t **)&h->d_wtree8, wtree8);
   if (e == cudaSuccess) {
     std::call_once(g_const_once, frbx::set_fft_constants);
     e = cudaGetLastError();
@@ -437,7 +459,7 @@ void frbx_destroy(frbx_handle *h) {
   if (!h) return;
   void *ptrs[] = {h->d_f,      h->d_f0,     h->d_wrot, h->d_tw_s, h->d_tw_m,     h->d_g,
                   h->d_sbd_tw, h->d_mbd_tw, h->d_slot, h->d_bimg, h->d_tree_tw, h->d_tree_slot, h->d_bimg8,
-                  h->d_wtree};
+                  h->d_wtree,  h->d_wtree8};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : h->ev)
@@ -541,7 +563,7 @@ int check_params(frbx_handle *h, const frbx_params *p, int n_bl, FitArgs *a) {
   if (!axis_window(Lm, p->mbd_win_ns, [&](int s) { return ((double)s * 1000.0) / ((double)Lm * dfg); },
                    &a->q_lo, &a->q_len))
     return fail(h, FRBX_EINVAL, "MBD window holds no grid cell");
-  if (p->kernel < 0 || p->kernel > 6) return fail(h, FRBX_EINVAL, "kernel must be 0 to 6");
+  if (p->kernel < 0 || p->kernel > 8) return fail(h, FRBX_EINVAL, "kernel must be 0 to 8");
   if (p->kernel == 3 || p->kernel == 5) {
     if (!h->d_bimg) return fail(h, FRBX_EUNSUPPORTED, "tensor-core fit needs Ls of 64 or 128, 2 Lm >= 32, N <= 64");
     if (a->m_len != Ls || a->q_len != Lm)
@@ -685,14 +707,18 @@ struct TreeRun {
   bool full = true;
   std::vector<int2> ser;  // (bl, d) of the series whose sweep fits the scan, baseline-major
   size_t chunk = 1, y_bytes = 0, a_bytes = 0;
+  size_t sc_off = 0;  // E4M3 form: offset of the per-AP scales in a buffer set
   int n_bl = 0;
   size_t need() const { return 2 * (y_bytes + a_bytes); }  // two buffer sets: chunks alternate
 };
 
 // Host planning: kernel arguments, series list and chunk size for `budget` bytes per set.
+// form: -1 = the FP32 tree (k_tree_mbd), else the tensor-core form of k_tree_mma (0 split BF16 x3,
+// 1 BF16, 2 E4M3).
 void plan_tree(const frbx_handle *h, const FitArgs &a, int nlev, const int32_t *windows, int n_win,
                const std::vector<int> &dkm, int n_bl, int T, int n_dm, const int *win_off, int S_tot, size_t budget,
-               bool mma, TreeRun *r) {
+               int form, TreeRun *r) {
+  const bool mma = form >= 0;
   frbx::TreeArgs &t = r->t;
   t = frbx::TreeArgs{};
   r->n_bl = n_bl;
@@ -724,12 +750,16 @@ void plan_tree(const frbx_handle *h, const FitArgs &a, int nlev, const int32_t *
   t.n_ktile = (T + t.k_per_cta - 1) / t.k_per_cta;
   t.y_series = (size_t)T * h->Ls * h->N;
   r->full = a.m_lo == 0 && a.m_len == h->Ls && a.q_lo == 0 && a.q_len == h->Lm;
-  if (mma) {  // tensor-core MBD pass: split A tiles per AP instead of FP32 rows
+  if (mma) {  // tensor-core MBD pass: A tiles per AP in their shared-memory image instead of FP32 rows
     t.mma = 1;
-    t.KA = (2 * h->N + 63) / 64;
-    t.tile_bytes = 2 * t.KA * 128 * 128;
-    t.wimg = (const unsigned char *)h->d_wtree;
-    t.w_bytes = h->wtree_bytes;
+    t.form = form;
+    t.KA = form == 2 ? (2 * h->N + 127) / 128 : (2 * h->N + 63) / 64;
+    t.k8_steps = (2 * h->N + 31) / 32;
+    t.tile_bytes = frbx::tree_mma_tile_bytes(form, h->N);
+    t.wimg = (const unsigned char *)(form == 2 ? h->d_wtree8 : h->d_wtree);
+    t.w_bytes = frbx::tree_mma_w_bytes(form, h->N);
+    // delay windows: rotate the SBD rows so the searched ones come first (in groups of 8)
+    t.rot = r->full ? 0 : (a.m_lo & ~7);
     t.n_qb = h->Lm / 32;
     t.log2Lm = a.log2Lm;
     t.err = (int *)h->errflag.p;
@@ -743,11 +773,14 @@ void plan_tree(const frbx_handle *h, const FitArgs &a, int nlev, const int32_t *
   for (int b = 0; b < n_bl; ++b)
     for (int d = 0; d < n_dm; ++d)
       if (T - dkm[(size_t)d] >= 1) r->ser.push_back(make_int2(b, d));
-  // per series: its transformed spectra and the deep anchors of its MBD CTAs
+  // per series: its transformed spectra, the E4M3 form's per-AP scales and the deep anchors of
+  // its MBD CTAs
   const size_t anc_per = mma ? 0 : sizeof(float2) * frbx::tree_anchor_floats(nlev) * t.n_mb * t.n_tt;
-  const size_t per = sizeof(float2) * t.y_series + anc_per;
+  const size_t sc_per = form == 2 ? sizeof(float) * (size_t)T : 0;
+  const size_t per = sizeof(float2) * t.y_series + sc_per + anc_per;
   r->chunk = std::max<size_t>(1, std::min(std::max<size_t>(r->ser.size(), 1), budget / per));
-  r->y_bytes = (sizeof(float2) * t.y_series * r->chunk + 255) & ~(size_t)255;
+  r->sc_off = (sizeof(float2) * t.y_series * r->chunk + 255) & ~(size_t)255;
+  r->y_bytes = r->sc_off + ((sc_per * r->chunk + 255) & ~(size_t)255);
   r->a_bytes = (anc_per * r->chunk + 255) & ~(size_t)255;
 }
 
@@ -785,6 +818,7 @@ int enqueue_tree(frbx_handle *h, const FitArgs &a, const TreeRun &r, const int2 
       tc.Y = (float2 *)base;
       tc.Yt = (const unsigned char *)base;
       tc.anc_g = (float2 *)(base + r.y_bytes);
+      tc.ascale = t.form == 2 ? (float *)(base + r.sc_off) : nullptr;
       tc.series = d_ser + c0;
       tc.n_s = (int)std::min(r.chunk, r.ser.size() - c0);
       cudaEvent_t *kev = timing ? h->tree_kev.data() + 4 * ci : nullptr;
@@ -797,7 +831,8 @@ int enqueue_tree(frbx_handle *h, const FitArgs &a, const TreeRun &r, const int2 
       if (e == cudaSuccess) e = cudaStreamWaitEvent(sB, evA[par], 0);
       if (e == cudaSuccess && kev) e = cudaEventRecord(kev[2], sB);
       if (e == cudaSuccess)
-        e = t.mma ? frbx::launch_tree_mma(tc, sB, &h->launches) : frbx::launch_tree_mbd(tc, r.full, sB, &h->launches);
+        e = t.mma ? frbx::launch_tree_mma(tc, r.full, sB, &h->launches)
+                  : frbx::launch_tree_mbd(tc, r.full, sB, &h->launches);
       if (e == cudaSuccess && kev) e = cudaEventRecord(kev[3], sB);
       if (e == cudaSuccess) e = cudaEventRecord(evB[par], sB);
       if (e == cudaErrorInvalidConfiguration) return fail(h, FRBX_EUNSUPPORTED, "window-tree fit does not fit this shape");
@@ -824,18 +859,19 @@ int tree_prepare(frbx_handle *h) {
 
 // frbx_search's window-tree fit: plan with a budget of a quarter of the free memory (at most
 // 16 GiB per buffer set), size the handle's scratch, upload the series list, enqueue.
-int run_fit_tree(frbx_handle *h, const FitArgs &a, int nlev, bool mma, const int32_t *windows, int n_win,
+int run_fit_tree(frbx_handle *h, const FitArgs &a, int nlev, int form, const int32_t *windows, int n_win,
                  const std::vector<int> &dkm, int n_bl, int T, int n_dm, const int *d_tab, int S_tot, cudaStream_t st) {
   size_t free_b = 0, total_b = 0;
   FRBX_CK(h, cudaMemGetInfo(&free_b, &total_b));
   const size_t budget = h->lim.tree_chunk_bytes > 0 ? (size_t)h->lim.tree_chunk_bytes
                                                     : std::min<size_t>((size_t)16 << 30, (free_b + h->ytree.bytes) / 4);
+  const bool mma = form >= 0;
   if (mma) {
     FRBX_CK(h, ensure(h, h->errflag, sizeof(int)));
     FRBX_CK(h, cudaMemsetAsync(h->errflag.p, 0, sizeof(int), st));
   }
   TreeRun r;
-  plan_tree(h, a, nlev, windows, n_win, dkm, n_bl, T, n_dm, d_tab + frbx::kMaxWin, S_tot, budget, mma, &r);
+  plan_tree(h, a, nlev, windows, n_win, dkm, n_bl, T, n_dm, d_tab + frbx::kMaxWin, S_tot, budget, form, &r);
   int rc = tree_prepare(h);
   if (rc) return rc;
   const size_t ser_bytes = (sizeof(int2) * std::max<size_t>(r.ser.size(), 1) + 255) & ~(size_t)255;
@@ -1023,7 +1059,7 @@ static int fit_segments_impl(frbx_handle *h, const void *vis, int32_t vis_on_dev
   FRBX_CK(h, ensure(h, h->seglist, sizeof(int32_t) * 4 * (size_t)n_seg));
   FRBX_CK(h, ensure(h, h->series, sizeof(frbx_seg) * (size_t)n_seg));
   FRBX_CK(h, cudaMemcpyAsync(h->seglist.p, segs, sizeof(int32_t) * 4 * (size_t)n_seg, cudaMemcpyHostToDevice, st));
-  if (p.kernel == 4 || p.kernel == 6) p.kernel = 0;  // explicit segment lists have no window structure to exploit
+  if (p.kernel == 4 || p.kernel >= 6) p.kernel = 0;  // explicit segment lists have no window structure to exploit
   fill_fit_tables(h, &a, dvis, T, n_dm);
   a.seg = (const int *)h->seglist.p;
   a.n_seg = n_seg;
@@ -1118,16 +1154,17 @@ static int search_impl(frbx_handle *h, const void *vis, int32_t vis_on_device, i
   FRBX_CK(h, cudaEventRecord(h->ev[2], st));
   int nlev = 0;
   const bool tree_ok = frbx::tree_supported(h->Ls, h->Lm, h->N, h->J, h->tree_s16, windows, n_win, &nlev);
-  const bool full_grid = a.m_lo == 0 && a.m_len == h->Ls && a.q_lo == 0 && a.q_len == h->Lm;
-  const bool tree_tc = tree_ok && full_grid && h->d_wtree && frbx::tree_mma_supported(h->Ls, h->Lm, h->N, h->J) &&
-                       frbx::tree_mma_fits(h->N, nlev);
-  if ((p.kernel == 4 && !tree_ok) || (p.kernel == 6 && !tree_tc))
+  // tensor-core window tree: kernel 6 (split BF16, FP32-equivalent), 7 (BF16), 8 (E4M3)
+  const bool tree_tc_shape = tree_ok && h->d_wtree && frbx::tree_mma_supported(h->Ls, h->Lm, h->N, h->J);
+  const int tc_form = p.kernel == 7 ? 1 : p.kernel == 8 ? 2 : 0;
+  const bool tree_tc = tree_tc_shape && frbx::tree_mma_fits(tc_form, h->N, nlev);
+  if ((p.kernel == 4 && !tree_ok) || (p.kernel >= 6 && !tree_tc))
     return fail(h, FRBX_EUNSUPPORTED,
                 "window-tree fit needs power-of-two windows <= 64 and Ls, Lm multiples of 32 (tensor cores: Ls 128, "
-                "2N <= 128, no delay windows)");
-  if (p.kernel == 4 || p.kernel == 6 || (p.kernel == 0 && tree_ok)) {
-    const bool mma = p.kernel == 6 || (p.kernel == 0 && tree_tc);
-    rc = run_fit_tree(h, a, nlev, mma, windows, n_win, dkm, n_bl, T, n_dm, d_tab, L.S_tot, st);
+                "2N <= 128, Lm a multiple of 32)");
+  if (p.kernel == 4 || p.kernel >= 6 || (p.kernel == 0 && tree_ok)) {
+    const int form = p.kernel >= 6 || (p.kernel == 0 && tree_tc) ? tc_form : -1;
+    rc = run_fit_tree(h, a, nlev, form, windows, n_win, dkm, n_bl, T, n_dm, d_tab, L.S_tot, st);
     if (rc) return rc;
   } else if (p.kernel == 3 || p.kernel == 5) {
     long long nv = 0;
@@ -1523,8 +1560,8 @@ extern "C" int frbx_search_batch(frbx_batch *b, const frbx_scan *scans, int32_t 
     const bool ok = frbx::tree_supported(h->Ls, h->Lm, h->N, h->J, h->tree_s16, windows, n_win, &nlev);
     const FitArgs &ag = fa[g];
     const bool tc_ok = ok && h->d_wtree && frbx::tree_mma_supported(h->Ls, h->Lm, h->N, h->J) &&
-                       frbx::tree_mma_fits(h->N, nlev) && ag.m_lo == 0 &&
-                       ag.m_len == h->Ls && ag.q_lo == 0 && ag.q_len == h->Lm;
+                       frbx::tree_mma_fits(0, h->N, nlev);
+    (void)ag;
     if ((p.kernel == 4 && !ok) || (p.kernel == 6 && !tc_ok))
       return bfail(b, FRBX_EUNSUPPORTED, "setup " + std::to_string(g) + ": window-tree fit does not apply");
     if (ok && (p.kernel == 0 || p.kernel == 4 || p.kernel == 6)) {
@@ -1703,7 +1740,7 @@ extern "C" int frbx_search_batch(frbx_batch *b, const frbx_scan *scans, int32_t 
       a.out = d_series + plan[(size_t)i].series_off;
       targs[(size_t)i] = a;
       plan_tree(h, a, tree_lev[(size_t)g], windows, n_win, dkm[(size_t)g], scans[i].n_bl, scans[i].T, n_dm,
-                a.win_off, a.S_tot, budget, tree_tc[(size_t)g] != 0, &truns[(size_t)i]);
+                a.win_off, a.S_tot, budget, tree_tc[(size_t)g] != 0 ? 0 : -1, &truns[(size_t)i]);
       need_h[(size_t)g] = std::max(need_h[(size_t)g], truns[(size_t)i].need());
       tser_off[(size_t)i] = tser_all.size();
       tser_all.insert(tser_all.end(), truns[(size_t)i].ser.begin(), truns[(size_t)i].ser.end());

@@ -166,7 +166,7 @@ struct TreeArgs {
   const float2 *tw;        // [NS/2][PM][2][2] MBD twiddles folded with the first DIF stage (0: empty)
   float2 *anc_g;           // deep window-tree anchors, one slice per MBD CTA
   // tensor-core MBD pass (3-term split BF16): Y as per-AP A tiles, W per block of 32 q
-  int mma;                 // 1: the SBD pass writes split tiles and the MBD pass is k_tree_mma
+  int mma;                 // 1: the SBD pass writes tensor-core A tiles and the MBD pass is k_tree_mma
   const unsigned char *Yt; // split tiles [n_s][T][tile_bytes] (aliases Y)
   size_t yt_series;        // bytes per series in Yt
   int KA;                  // 64-wide K atoms per tile row (K = 2N)
@@ -179,12 +179,18 @@ struct TreeArgs {
   long long timeout;       // clock cycles per pipeline wait
   long long drain_timeout; // clock cycles per wait that drains copies / MMAs in flight before exit
   int hold;                // test aid: the loader issues no copies, so the pipeline waits run out
+  int form;                // MBD product of k_tree_mma: 0 split BF16 x3, 1 BF16, 2 E4M3
+  int k8_steps;            // E4M3 form: K = 32 steps per AP, (2N + 31) / 32
+  float *ascale;           // E4M3 form: 1 / s of every AP, [n_s][T] (s: power-of-two scale of A)
+  int rot;                 // delay windows: tile row r holds SBD row (r + rot) mod Ls (multiple of 8)
   int n_abuf;              // A-tile ring depth of k_tree_mma (set by its launcher)
   int n_sanc;              // window-tree anchor levels of k_tree_mma in shared memory (set by its launcher)
 };
 bool tree_mma_supported(int Ls, int Lm, int N, int J);
-bool tree_mma_fits(int N, int nlev);  // shared memory holds W, the A ring and the deep anchors
-cudaError_t launch_tree_mma(const TreeArgs &t, cudaStream_t st, int64_t *launches);
+bool tree_mma_fits(int form, int N, int nlev);  // shared memory holds W, the A ring and the deep anchors
+int tree_mma_tile_bytes(int form, int N);        // one AP's A operand in its shared-memory image
+int tree_mma_w_bytes(int form, int N);           // the DFT operand of one block of 32 q
+cudaError_t launch_tree_mma(const TreeArgs &t, bool full, cudaStream_t st, int64_t *launches);
 bool tree_supported(int Ls, int Lm, int N, int J, int s16, const int *windows, int n_win, int *nlev);
 size_t tree_anchor_floats(int nlev);  // float2 per MBD CTA in TreeArgs::anc_g
 cudaError_t launch_tree_sbd(const FitArgs &a, const TreeArgs &t, cudaStream_t st, int64_t *launches);
@@ -267,6 +273,7 @@ struct frbx_handle {
   void *d_bimg = nullptr;  // BF16 DFT matrix image for the tensor-core fit (if supported)
   void *d_bimg8 = nullptr;  // the same matrix in E4M3
   void *d_wtree = nullptr;  // window-tree tensor-core fit: split-BF16 DFT blocks of 32 q
+  void *d_wtree8 = nullptr; // the same blocks in E4M3 (kernel 8)
   int wtree_bytes = 0;      // per block
   int b_bytes = 0, b_bytes8 = 0, b_atom_bytes = 0, KA = 0, NC = 0;
   int *d_g = nullptr, *d_slot = nullptr;

@@ -29,6 +29,7 @@
 //              merged across blocks by a 64-bit atomicMax on (|G|^2 bits, ~cell index) in the
 //              series buffer, which k_tree_finalize turns into frbx_seg records.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include "fit_common.cuh"
 #include "fft32.cuh"
@@ -56,22 +57,26 @@ __host__ __device__ inline size_t tree_smem_bytes(int NS, int PM, int RB, int nl
 }
 
 // ----------------------------------------------------------------------------- SBD pass
-// kSplit: instead of FP32 rows, each AP's output is the tensor-core A operand of k_tree_mma in
-// its shared-memory image: A_hi = bf16(Y) then A_lo = bf16(Y - A_hi), 128 rows x K = 2N
-// (Re Y of the channels, then Im Y), 128-byte swizzled K atoms.
-template <bool kSplit>
+// kOut 0: FP32 rows Y[m][n] for k_tree_mbd.  kOut 1..3: each AP's output is the tensor-core A
+// operand of k_tree_mma in its shared-memory image, 128 rows x K = 2N (Re Y of the channels, then
+// Im Y), 128-byte swizzled K atoms: 1 = A_hi = bf16(Y) then A_lo = bf16(Y - A_hi); 2 = A_hi only;
+// 3 = E4M3 of s Y, s the power of two with s L1 <= 448 (L1 = the L1 norm of the AP's dedispersed
+// spectrum, which bounds every |Re Y|, |Im Y|), 1 / s stored in t.ascale.  Tile row r holds SBD
+// row (r + t.rot) mod Ls (rotation for delay windows; 0 for the whole grid).
+template <int kOut>
 __global__ void __launch_bounds__(kTreeThreads, 4)
     k_tree_sbd(const __grid_constant__ FitArgs a, const __grid_constant__ TreeArgs t) {
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ float red_l1[kTreeThreads / 32];
   const int N = a.N, Ls = a.Ls, PS = Ls >> 5, lps = __ffs(PS) - 1;
   const int JP = a.J1 * 32, xs = JP + 1;
-  const int stage = kSplit ? t.tile_bytes : (int)sizeof(float2) * Ls * N;  // one AP of output
-  float2 *Ys = reinterpret_cast<float2 *>(smem);                          // [Ls][N] or the tiles
+  const int stage = kOut ? t.tile_bytes : (int)sizeof(float2) * Ls * N;  // one AP of output
+  float2 *Ys = reinterpret_cast<float2 *>(smem);                        // [Ls][N] or the tiles
   unsigned char *Yb = smem;
   float2 *X = reinterpret_cast<float2 *>(smem + stage);  // [N][xs]
   float2 *stw = X + N * xs;                              // [PS][xs]
   for (int i = threadIdx.x; i < N * xs; i += blockDim.x) X[i] = make_float2(0.f, 0.f);
-  if (kSplit)  // K columns beyond 2N stay zero
+  if (kOut)  // K columns beyond 2N stay zero
     for (int i = threadIdx.x; i < stage / 16; i += blockDim.x) reinterpret_cast<uint4 *>(Yb)[i] = make_uint4(0, 0, 0, 0);
   for (int i = threadIdx.x; i < PS * JP; i += blockDim.x) {
     const int r = i / JP, c = i - r * JP;
@@ -83,9 +88,10 @@ __global__ void __launch_bounds__(kTreeThreads, 4)
   const int kd = a.T - t.dk_max[sd.y];
   const int k_lo = tile * t.k_per_cta, k_hi = min(kd, k_lo + t.k_per_cta);
   const int *dk = a.dk + (size_t)sd.y * a.C;
-  float4 *Yout = kSplit ? reinterpret_cast<float4 *>(const_cast<unsigned char *>(t.Yt) + (size_t)s * t.yt_series)
-                        : reinterpret_cast<float4 *>(t.Y + (size_t)s * t.y_series);
+  float4 *Yout = kOut ? reinterpret_cast<float4 *>(const_cast<unsigned char *>(t.Yt) + (size_t)s * t.yt_series)
+                      : reinterpret_cast<float4 *>(t.Y + (size_t)s * t.y_series);
   const int row4 = stage / 16;  // float4 per AP
+  const int rot8 = t.rot >> 3;  // rotation in groups of 8 rows
   // this thread's points p = tid + blockDim i: channel n and point j stepped without a division
   const int dn = (int)blockDim.x / a.J, dj = (int)blockDim.x - dn * a.J;
   const int n0 = (int)threadIdx.x / a.J, j0 = (int)threadIdx.x - n0 * a.J;
@@ -95,6 +101,7 @@ __global__ void __launch_bounds__(kTreeThreads, 4)
     // independent cube loads in flight per thread (the shift-table row stays in L1)
     const size_t row0 = (size_t)sd.x * a.T + k;
     int n = n0, j = j0;
+    float l1 = 0.f;
     for (int p0 = threadIdx.x; p0 < a.C; p0 += blockDim.x * kSbdBatch) {
       float2 v[kSbdBatch];
 #pragma unroll
@@ -105,7 +112,11 @@ __global__ void __launch_bounds__(kTreeThreads, 4)
 #pragma unroll
       for (int q = 0; q < kSbdBatch; ++q) {
         const int p = p0 + q * (int)blockDim.x;
-        if (p < a.C) X[n * xs + j] = cmul(v[q], __ldg(a.wrot + p));
+        if (p < a.C) {
+          const float2 x = cmul(v[q], __ldg(a.wrot + p));
+          X[n * xs + j] = x;
+          if (kOut == 3) l1 += fabsf(x.x) + fabsf(x.y);
+        }
         n += dn;
         j += dj;
         if (j >= a.J) {
@@ -114,7 +125,22 @@ __global__ void __launch_bounds__(kTreeThreads, 4)
         }
       }
     }
+    if (kOut == 3) {
+#pragma unroll
+      for (int off = 16; off; off >>= 1) l1 += __shfl_xor_sync(0xffffffffu, l1, off);
+      if ((threadIdx.x & 31) == 0) red_l1[threadIdx.x >> 5] = l1;
+    }
     __syncthreads();
+    float sc = 1.f;
+    if (kOut == 3) {
+      float tot = 0.f;
+#pragma unroll
+      for (int w = 0; w < kTreeThreads / 32; ++w) tot += red_l1[w];
+      int ex = 1;
+      if (tot > 1e-30f) frexpf(448.f / tot, &ex);
+      sc = ldexpf(1.f, max(-100, min(100, ex - 1)));
+      if (threadIdx.x == 0) t.ascale[(size_t)s * a.T + k] = 1.f / sc;
+    }
     // SBD transform of every channel, task (n, m1); row m = m1 + PS m2 holds the channel slots
     for (int u = threadIdx.x; u < N * PS; u += blockDim.x) {
       const int n = u >> lps, m1 = u & (PS - 1);
@@ -128,11 +154,11 @@ __global__ void __launch_bounds__(kTreeThreads, 4)
         for (int j2 = 0; j2 < 32; ++j2) A[j2] = cfma(A[j2], xr[j1 * 32 + j2], wr[j1 * 32 + j2]);
       }
       fft32_dif(A);
-      if (kSplit) {
+      if (kOut == 1 || kOut == 2) {
         const int half = t.tile_bytes / 2;
-        // Ls = 128 rows (PS = 4): row = m1 + 4 b with b = bitrev5(i), so row / 8 = b / 2 and
-        // row % 8 = m1 + 4 (b % 2); the swizzled offsets of columns n and N + n for even and odd
-        // b are fixed per thread, and each element adds its 1 KB row group
+        // Ls = 128 rows (PS = 4): row = m1 + 4 b with b = bitrev5(i), so (row - rot) / 8 = b / 2 - rot / 8
+        // and row % 8 = m1 + 4 (b % 2); the swizzled offsets of columns n and N + n for even and
+        // odd b are fixed per thread, and each element adds its 1 KB row group
         uint32_t o_re[2] = {0u, 0u}, o_im[2] = {0u, 0u};
         if (PS == 4) {
 #pragma unroll
@@ -143,16 +169,37 @@ __global__ void __launch_bounds__(kTreeThreads, 4)
         }
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
-          const int b = bitrev5(i), row = m1 + PS * b;
+          const int b = bitrev5(i), row = (m1 + PS * b - t.rot) & (Ls - 1);
           const __nv_bfloat16 rh = __float2bfloat16_rn(A[i].x), ih = __float2bfloat16_rn(A[i].y);
-          const __nv_bfloat16 rl = __float2bfloat16_rn(A[i].x - __bfloat162float(rh));
-          const __nv_bfloat16 il = __float2bfloat16_rn(A[i].y - __bfloat162float(ih));
-          const uint32_t orr = PS == 4 ? o_re[b & 1] + (uint32_t)(b >> 1) * 1024u : tc::a_offset(row, n);
-          const uint32_t oi = PS == 4 ? o_im[b & 1] + (uint32_t)(b >> 1) * 1024u : tc::a_offset(row, N + n);
+          const uint32_t grp = (uint32_t)(((b >> 1) - rot8) & 15) * 1024u;
+          const uint32_t orr = PS == 4 ? o_re[b & 1] + grp : tc::a_offset(row, n);
+          const uint32_t oi = PS == 4 ? o_im[b & 1] + grp : tc::a_offset(row, N + n);
           *reinterpret_cast<__nv_bfloat16 *>(Yb + orr) = rh;
           *reinterpret_cast<__nv_bfloat16 *>(Yb + oi) = ih;
-          *reinterpret_cast<__nv_bfloat16 *>(Yb + half + orr) = rl;
-          *reinterpret_cast<__nv_bfloat16 *>(Yb + half + oi) = il;
+          if (kOut == 1) {
+            const __nv_bfloat16 rl = __float2bfloat16_rn(A[i].x - __bfloat162float(rh));
+            const __nv_bfloat16 il = __float2bfloat16_rn(A[i].y - __bfloat162float(ih));
+            *reinterpret_cast<__nv_bfloat16 *>(Yb + half + orr) = rl;
+            *reinterpret_cast<__nv_bfloat16 *>(Yb + half + oi) = il;
+          }
+        }
+      } else if (kOut == 3) {
+        uint32_t o_re[2] = {0u, 0u}, o_im[2] = {0u, 0u};
+        if (PS == 4) {
+#pragma unroll
+          for (int odd = 0; odd < 2; ++odd) {
+            o_re[odd] = tc::a_offset8(m1 + 4 * odd, n);
+            o_im[odd] = tc::a_offset8(m1 + 4 * odd, N + n);
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const int b = bitrev5(i), row = (m1 + PS * b - t.rot) & (Ls - 1);
+          const uint32_t grp = (uint32_t)(((b >> 1) - rot8) & 15) * 1024u;
+          const uint32_t orr = PS == 4 ? o_re[b & 1] + grp : tc::a_offset8(row, n);
+          const uint32_t oi = PS == 4 ? o_im[b & 1] + grp : tc::a_offset8(row, N + n);
+          Yb[orr] = (unsigned char)__nv_cvt_float_to_fp8(A[i].x * sc, __NV_SATFINITE, __NV_E4M3);
+          Yb[oi] = (unsigned char)__nv_cvt_float_to_fp8(A[i].y * sc, __NV_SATFINITE, __NV_E4M3);
         }
       } else {
 #pragma unroll
@@ -414,7 +461,8 @@ cudaError_t launch_tree_sbd(const FitArgs &a, const TreeArgs &t, cudaStream_t st
   if (smem > max_smem_optin()) return cudaErrorInvalidConfiguration;
   const long long nb = (long long)t.n_s * t.n_ktile;
   if (nb <= 0) return cudaSuccess;
-  auto kern = t.mma ? k_tree_sbd<true> : k_tree_sbd<false>;
+  if (!t.mma && t.rot != 0) return cudaErrorInvalidValue;
+  auto kern = !t.mma ? k_tree_sbd<0> : t.form == 0 ? k_tree_sbd<1> : t.form == 1 ? k_tree_sbd<2> : k_tree_sbd<3>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<(unsigned)nb, kTreeThreads, smem, st>>>(a, t);

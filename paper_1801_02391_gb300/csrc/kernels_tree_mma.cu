@@ -26,9 +26,20 @@
 //          anchor, used every 32 APs, in shared memory), and merge every emitted segment's
 //          warp maximum into the series by a 64-bit atomicMax, as k_tree_mbd does per block:
 //          the warps never wait for one another.
+// Two lower-precision forms of the same tree run one product per AP instead of three: kernel 7
+// multiplies A_hi by W_hi (BF16, about 4e-3 relative on |G|), kernel 8 multiplies E4M3 operands
+// with kind::f8f6f4 (about 6e-2 relative), A scaled per AP by the power of two s with
+// s L1 <= 448 (L1 the L1 norm of the AP's dedispersed spectrum, which bounds every |Re Y|,
+// |Im Y|); the epilogue multiplies G_1(k) by 1 / s before it enters the tree, so windows sum
+// unscaled matrices.
+// With delay search windows the SBD pass stores the rows rotated by t.rot (a multiple of 8),
+// tile row r = (m - rot) mod Ls, so the searched rows sit in the first row quarters: warps whose
+// rows are all outside the SBD window only release their slots, cells outside the windows are
+// masked, and CTAs whose 32 q lie outside the MBD window exit at once.
 // Every wait is bounded: on timeout the kernel records FRBX_ETIMEOUT, drains and frees its
 // tensor memory.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include "fit_common.cuh"
 #include "tc_common.cuh"
@@ -42,23 +53,39 @@ constexpr int kTmCols = 2 * kTmNQ;          // Re G of the 32 q, then Im G
 constexpr int kTmMaxABufs = 3;              // ring of one-AP A tiles (2 where shared memory is short)
 constexpr int kTmTmemCols = 512;            // accumulator slots, then the tensor-memory anchors
 constexpr int kTmMaxLev = 6;
-constexpr int kTmWAtom = kTmCols * 128;     // 64 rows of one 64-wide K atom of W (8 KB)
-constexpr int kTmSlotCols = 2 * kTmCols;    // one accumulator slot: [A_hi W_hi | A_hi W_lo + A_lo W_hi]
+constexpr int kTmWAtom = kTmCols * 128;     // 64 rows of one 128-byte K atom of W (8 KB)
 constexpr int kTmAncBytes = tc::kRows * kTmCols * 4;  // one anchor level in shared memory (32 KB)
 // configuration of the launched instance: epilogue warps (8 or 16) and accumulator slots
 constexpr int kTmEpi = 8;
 constexpr int kTmSlots = 2;
 
-__host__ __device__ constexpr int tm_tmem_anchors(int slots) { return (kTmTmemCols - slots * kTmSlotCols) / kTmCols; }
+// forms of the MBD product (TreeArgs::form)
+constexpr int kFormSplit = 0;  // A_hi W_hi + A_hi W_lo + A_lo W_hi in BF16 (FP32-equivalent)
+constexpr int kFormBf16 = 1;   // A_hi W_hi
+constexpr int kFormFp8 = 2;    // E4M3 x E4M3, A scaled per AP
+
+// one accumulator slot: [A_hi W_hi | A_hi W_lo + A_lo W_hi] for the split form, else one product
+__host__ __device__ constexpr int tm_slot_cols(int form) { return form == kFormSplit ? 2 * kTmCols : kTmCols; }
+__host__ __device__ constexpr int tm_tmem_anchors(int form, int slots) {
+  return (kTmTmemCols - slots * tm_slot_cols(form)) / kTmCols;
+}
+// K atoms (128 bytes of K per row) of the A tile and of W, and their bytes
+__host__ __device__ inline int tm_katoms(int form, int N) { return form == kFormFp8 ? (2 * N + 127) / 128 : (2 * N + 63) / 64; }
+__host__ __device__ inline int tm_tile_bytes(int form, int N) {
+  return (form == kFormSplit ? 2 : 1) * tm_katoms(form, N) * tc::kAtomBytes;
+}
+__host__ __device__ inline int tm_w_bytes(int form, int N) {
+  return (form == kFormFp8 ? 1 : 2) * tm_katoms(form, N) * kTmWAtom;  // BF16: hi rows then lo rows per atom
+}
 size_t tm_smem_bytes(int w_bytes, int tile_bytes, int n_abuf, int n_sanc) {
   return (size_t)((w_bytes + 1023) & ~1023) + (size_t)n_abuf * tile_bytes + (size_t)n_sanc * kTmAncBytes + 1024;
 }
 // Memory plan: the anchor levels go to tensor memory as far as it has room beside the slots (a
 // visit moves 64 KB, which shared memory's bandwidth makes slower), the deeper rest to shared
 // memory after W and the deepest A-tile ring that fits.  Returns false when nothing fits.
-bool tm_plan(int KA, int nlev, int *n_abuf, int *n_sanc) {
-  const int w_bytes = 2 * KA * kTmWAtom, tile_bytes = 2 * KA * tc::kAtomBytes;
-  *n_sanc = max(0, nlev - 1 - tm_tmem_anchors(kTmSlots));
+bool tm_plan(int form, int N, int nlev, int *n_abuf, int *n_sanc) {
+  const int w_bytes = tm_w_bytes(form, N), tile_bytes = tm_tile_bytes(form, N);
+  *n_sanc = max(0, nlev - 1 - tm_tmem_anchors(form, kTmSlots));
   for (int nb = kTmMaxABufs; nb >= 2; --nb)
     if (tm_smem_bytes(w_bytes, tile_bytes, nb, *n_sanc) + 512 <= max_smem_optin()) {  // 512: static
       *n_abuf = nb;
@@ -142,20 +169,30 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t ad, uint64_t 
   asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
                ::"r"(d_tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(accum) : "memory");
 }
+// D = F32, A = B = E4M3 (format code 0), K-major
+__device__ __forceinline__ uint32_t idesc_e4m3(int n) {
+  return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(tc::kRows >> 4) << 24);
+}
+__device__ __forceinline__ void mma_e4m3(uint32_t d_tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t accum) {
+  asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n"
+               ::"r"(d_tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(accum) : "memory");
+}
 
 }  // namespace
 
 // kEpi epilogue warps, then the MMA warp and the loader warp.  Tensor memory: kSlots accumulator
-// slots of 128 columns at 128 i, then the anchors of levels 2, 3, ... at 64-column steps.
-// Shared memory: W, the A-tile ring (t.n_abuf deep), then the t.n_sanc deepest anchor levels as
-// [level][16 column quads][128 rows] float4.
-template <int kEpi, int kSlots>
+// slots (128 columns for the split form, else 64), then the anchors of levels 2, 3, ... at
+// 64-column steps.  Shared memory: W, the A-tile ring (t.n_abuf deep), then the t.n_sanc deepest
+// anchor levels as [level][16 column quads][128 rows] float4.  kForm: the MBD product (above);
+// kFull: the whole delay grid is searched (no windows, no row rotation).
+template <int kEpi, int kSlots, int kForm, bool kFull>
 __global__ void __launch_bounds__((kEpi + 2) * 32, 1) k_tree_mma(const __grid_constant__ TreeArgs t) {
   constexpr int kMmaWarp = kEpi, kLoadWarp = kEpi + 1;
   constexpr int kQ = kTmNQ / (kEpi / 4);   // MBD columns per epilogue thread (16 or 8)
   constexpr int kP = kQ / 2;               // packed pairs
-  constexpr int kAnc = kSlots * kTmSlotCols;
-  static_assert(tm_tmem_anchors(kSlots) >= 0, "tensor memory");
+  constexpr int kSlotCols = tm_slot_cols(kForm);
+  constexpr int kAnc = kSlots * kSlotCols;
+  static_assert(tm_tmem_anchors(kForm, kSlots) >= 0, "tensor memory");
   extern __shared__ unsigned char smem_raw[];
   unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ uint64_t bar_afull[kTmMaxABufs], bar_aempty[kTmMaxABufs], bar_accfull[kSlots], bar_accempty[kSlots],
@@ -173,6 +210,14 @@ __global__ void __launch_bounds__((kEpi + 2) * 32, 1) k_tree_mma(const __grid_co
   const int kd = t.T - t.dk_max[sd.y];
   const int kb = tt * t.TT;
   if (kb >= kd) return;  // every segment starting here runs past the scan (uniform)
+  // searched q of this block (bit j: q = 32 qb + j); none: nothing to do (uniform)
+  unsigned qbmask = 0xffffffffu;
+  if (!kFull) {
+    qbmask = 0u;
+    for (int j = 0; j < kTmNQ; ++j)
+      if ((((qb * kTmNQ + j) - t.q_lo) & (t.Lm - 1)) < t.q_len) qbmask |= 1u << j;
+    if (qbmask == 0u) return;
+  }
   const int ke = min(kd, kb + t.TT + (1 << t.nlev) - 1);
   const int n_ap = ke - kb;
   const int nbuf = t.n_abuf, n_tanc = max(t.nlev - 1, 0) - t.n_sanc;  // anchor levels in tensor memory
@@ -242,7 +287,7 @@ __global__ void __launch_bounds__((kEpi + 2) * 32, 1) k_tree_mma(const __grid_co
     // per-instruction moves into uniform registers); one elected lane issues the MMAs and
     // commits, which keeps the issue rate at the tensor pipe's pace.
     const bool leader = tc::elect_one();
-    const uint32_t id64 = idesc_bf16(kTmCols), id128 = idesc_bf16(2 * kTmCols);
+    const uint32_t id64 = idesc_bf16(kTmCols), id128 = idesc_bf16(2 * kTmCols), id8 = idesc_e4m3(kTmCols);
     // descriptors of the K steps differ only in the start address field (address / 16, in
     // the low 14 bits, which shared-memory offsets below 256 KB never carry out of)
     const uint32_t a_half16 = (uint32_t)(t.KA * tc::kAtomBytes) >> 4;
@@ -259,23 +304,42 @@ __global__ void __launch_bounds__((kEpi + 2) * 32, 1) k_tree_mma(const __grid_co
       }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint64_t a0 = sa0 + (uint64_t)(b * tile16);
-      const uint32_t d_tmem = tmem + (uint32_t)(slot * kTmSlotCols);
+      const uint32_t d_tmem = tmem + (uint32_t)(slot * kSlotCols);
       if (leader) {
-        // D[0:64] = A_hi W_hi, D[64:128] = A_hi W_lo (one N = 128 MMA per K step) + A_lo W_hi
-        for (int ka = 0; ka < t.KA; ++ka) {
+        if constexpr (kForm == kFormSplit) {
+          // D[0:64] = A_hi W_hi, D[64:128] = A_hi W_lo (one N = 128 MMA per K step) + A_lo W_hi
+          for (int ka = 0; ka < t.KA; ++ka) {
 #pragma unroll
-          for (int k4 = 0; k4 < 4; ++k4) {
-            const uint32_t ao = (uint32_t)((ka * tc::kAtomBytes + k4 * 32) >> 4);
-            const uint32_t bo = (uint32_t)((ka * 2 * kTmWAtom + k4 * 32) >> 4);
-            mma_bf16(d_tmem, a0 + ao, w0 + bo, id128, (ka | k4) ? 1u : 0u);
+            for (int k4 = 0; k4 < 4; ++k4) {
+              const uint32_t ao = (uint32_t)((ka * tc::kAtomBytes + k4 * 32) >> 4);
+              const uint32_t bo = (uint32_t)((ka * 2 * kTmWAtom + k4 * 32) >> 4);
+              mma_bf16(d_tmem, a0 + ao, w0 + bo, id128, (ka | k4) ? 1u : 0u);
+            }
           }
-        }
-        for (int ka = 0; ka < t.KA; ++ka) {
+          for (int ka = 0; ka < t.KA; ++ka) {
 #pragma unroll
-          for (int k4 = 0; k4 < 4; ++k4) {
-            const uint32_t ao = (uint32_t)((ka * tc::kAtomBytes + k4 * 32) >> 4);
-            const uint32_t bo = (uint32_t)((ka * 2 * kTmWAtom + k4 * 32) >> 4);
-            mma_bf16(d_tmem + (uint32_t)kTmCols, a0 + a_half16 + ao, w0 + bo, id64, 1u);
+            for (int k4 = 0; k4 < 4; ++k4) {
+              const uint32_t ao = (uint32_t)((ka * tc::kAtomBytes + k4 * 32) >> 4);
+              const uint32_t bo = (uint32_t)((ka * 2 * kTmWAtom + k4 * 32) >> 4);
+              mma_bf16(d_tmem + (uint32_t)kTmCols, a0 + a_half16 + ao, w0 + bo, id64, 1u);
+            }
+          }
+        } else if constexpr (kForm == kFormBf16) {
+          // D = A_hi W_hi (the hi rows of each W atom)
+          for (int ka = 0; ka < t.KA; ++ka) {
+#pragma unroll
+            for (int k4 = 0; k4 < 4; ++k4) {
+              const uint32_t ao = (uint32_t)((ka * tc::kAtomBytes + k4 * 32) >> 4);
+              const uint32_t bo = (uint32_t)((ka * 2 * kTmWAtom + k4 * 32) >> 4);
+              mma_bf16(d_tmem, a0 + ao, w0 + bo, id64, (ka | k4) ? 1u : 0u);
+            }
+          }
+        } else {
+          // D = A8 W8 (E4M3, K = 32 per instruction, 32 bytes of each 128-byte row)
+          for (int kk = 0; kk < t.k8_steps; ++kk) {
+            const uint32_t ao = (uint32_t)(((kk >> 2) * tc::kAtomBytes + (kk & 3) * 32) >> 4);
+            const uint32_t bo = (uint32_t)(((kk >> 2) * kTmWAtom + (kk & 3) * 32) >> 4);
+            mma_e4m3(d_tmem, a0 + ao, w0 + bo, id8, kk ? 1u : 0u);
           }
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
@@ -305,7 +369,30 @@ __global__ void __launch_bounds__((kEpi + 2) * 32, 1) k_tree_mma(const __grid_co
     const int quarter = warp & 3, part = warp >> 2;
     const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
     const uint32_t c_re = (uint32_t)(kQ * part), c_im = (uint32_t)(kTmNQ + kQ * part);
-    const unsigned idx0 = (unsigned)((quarter * 32) * t.Lm + qb * kTmNQ + kQ * part);  // cell 0 of lane 0
+    // this lane's SBD row m (tile row quarter * 32 + lane, rotated by t.rot) and its first cell
+    const int m_row = (quarter * 32 + lane + t.rot) & (t.Ls - 1);
+    const unsigned idx_base = (unsigned)(m_row * t.Lm + qb * kTmNQ + kQ * part);
+    // delay windows: the lane's row is searched, and which of its kQ cells
+    const bool row_on = kFull || (((m_row - t.m_lo) & (t.Ls - 1)) < t.m_len);
+    const unsigned qmask = kFull ? 0xffffffffu : (qbmask >> (kQ * part)) & ((1u << kQ) - 1u);
+    if (!kFull && !__any_sync(0xffffffffu, row_on && qmask != 0u)) {
+      // nothing of this warp is searched: it only hands each slot back
+      bool ok = true;
+      for (int i = 0, slot = 0, sph = 0; i < n_ap && ok; ++i) {
+        if (!__all_sync(0xffffffffu, tc::mbar_wait(&bar_accfull[slot], (uint32_t)sph, abortp, t.timeout))) {
+          ok = false;
+          break;
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&bar_accempty[slot]);
+        if (++slot == kSlots) {
+          slot = 0;
+          sph ^= 1;
+        }
+      }
+      if (!ok) *abortp = 1;
+    } else {
     // this thread's quads of a shared-memory anchor: re at kQ/4 part + u, im at 8 + kQ/4 part + u
     ulonglong2 *my_anc = sAnc + (size_t)(kQ / 4 * part) * tc::kRows + quarter * 32 + lane;
     unsigned long long *keys = t.keys + ((size_t)sd.x * t.n_dm + sd.y) * t.S_tot;
@@ -344,6 +431,10 @@ __global__ void __launch_bounds__((kEpi + 2) * 32, 1) k_tree_mma(const __grid_co
         kf[2 * p] = __uint_as_float((lo & ~63u) | (unsigned)(31 - 2 * p));
         kf[2 * p + 1] = __uint_as_float((hi & ~63u) | (unsigned)(30 - 2 * p));
       }
+      if (!kFull && qmask != (1u << kQ) - 1u) {  // cells outside the MBD window (uniform per warp)
+#pragma unroll
+        for (int j = 0; j < kQ; ++j) kf[j] = (qmask >> j) & 1u ? kf[j] : 0.f;
+      }
       float top;
       if constexpr (kQ == 16) {
         float m5[5];
@@ -354,10 +445,10 @@ __global__ void __launch_bounds__((kEpi + 2) * 32, 1) k_tree_mma(const __grid_co
         static_assert(kQ == 8, "8 or 16 cells per thread");
         top = fmax3(fmax3(kf[0], kf[1], kf[2]), fmax3(kf[3], kf[4], kf[5]), fmaxf(kf[6], kf[7]));
       }
-      const unsigned tkey = __float_as_uint(top);
+      const unsigned tkey = row_on ? __float_as_uint(top) : 0u;
       const unsigned wmax = __reduce_max_sync(0xffffffffu, tkey);
-      if (tkey == wmax) {
-        const unsigned idx = idx0 + (unsigned)lane * (unsigned)t.Lm + (31u - (wmax & 63u));
+      if (tkey == wmax && wmax != 0u) {
+        const unsigned idx = idx_base + (31u - (wmax & 63u));
         // slot of the segment: windows of 2^e APs start every 2^(e-1) APs (every AP for e = 0)
         atomicMax(keys + woff[e] + (k0 >> (e > 0 ? e - 1 : 0)),
                   ((unsigned long long)(wmax & ~63u) << 32) | (unsigned long long)(~idx));
@@ -370,11 +461,15 @@ __global__ void __launch_bounds__((kEpi + 2) * 32, 1) k_tree_mma(const __grid_co
       if (!__all_sync(0xffffffffu, tc::mbar_wait(&bar_accfull[slot], sph, abortp, t.timeout))) return false;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       uint64_t lre[kP], lim[kP];
-      const uint32_t cur = lane_base + (uint32_t)(slot * kTmSlotCols);
+      const uint32_t cur = lane_base + (uint32_t)(slot * kSlotCols);
       tm_ld<kQ>(cur + c_re, cre);
       tm_ld<kQ>(cur + c_im, cim);
-      tm_ld<kQ>(cur + kTmCols + c_re, lre);
-      tm_ld<kQ>(cur + kTmCols + c_im, lim);
+      if constexpr (kForm == kFormSplit) {
+        tm_ld<kQ>(cur + kTmCols + c_re, lre);
+        tm_ld<kQ>(cur + kTmCols + c_im, lim);
+      }
+      float inv_s = 1.f;  // E4M3 form: the AP's A was scaled by s, a power of two
+      if constexpr (kForm == kFormFp8) inv_s = __ldg(t.ascale + (size_t)s * t.T + k);
       // levels whose window ends at k, and which of them emit a segment of this time tile
       // (uniform across the CTA)
       const int E = t.nlev == 0 ? 0 : min(t.nlev, __ffs(k + 1));
@@ -385,10 +480,19 @@ __global__ void __launch_bounds__((kEpi + 2) * 32, 1) k_tree_mma(const __grid_co
         if (e <= E && woff[e] >= 0 && k0 >= kb && k0 < kb + t.TT) em |= 1u << e;
       }
       tm_wait_ld();
+      if constexpr (kForm == kFormSplit) {
 #pragma unroll
-      for (int p = 0; p < kP; ++p) {
-        cre[p] = add2(cre[p], lre[p]);
-        cim[p] = add2(cim[p], lim[p]);
+        for (int p = 0; p < kP; ++p) {
+          cre[p] = add2(cre[p], lre[p]);
+          cim[p] = add2(cim[p], lim[p]);
+        }
+      } else if constexpr (kForm == kFormFp8) {
+        const uint64_t iv = pk(__float_as_uint(inv_s), __float_as_uint(inv_s));
+#pragma unroll
+        for (int p = 0; p < kP; ++p) {
+          cre[p] = mul2(cre[p], iv);
+          cim[p] = mul2(cim[p], iv);
+        }
       }
       // G_1(k) is in the warp's registers: its slot may take AP k + kSlots.  One arrival per
       // warp: 256 arrivals on one mbarrier serialise as shared-memory atomics.
@@ -450,6 +554,7 @@ __global__ void __launch_bounds__((kEpi + 2) * 32, 1) k_tree_mma(const __grid_co
     }
     if (ok && i < n_ap && !one_ap(i, 0, sph, gb_re, gb_im, ga_re, ga_im)) ok = false;
     if (!ok) *abortp = 1;
+    }
   }
 
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -463,27 +568,47 @@ bool tree_mma_supported(int Ls, int Lm, int N, int J) {
   return Ls == tc::kRows && J <= Ls && Lm % kTmNQ == 0 && 2 * N <= 128;
 }
 
-bool tree_mma_fits(int N, int nlev) {
+bool tree_mma_fits(int form, int N, int nlev) {
   int nb, ns;
-  return nlev >= 0 && nlev <= kTmMaxLev && tm_plan((2 * N + 63) / 64, nlev, &nb, &ns);
+  return form >= kFormSplit && form <= kFormFp8 && nlev >= 0 && nlev <= kTmMaxLev && tm_plan(form, N, nlev, &nb, &ns);
 }
 
-cudaError_t launch_tree_mma(const TreeArgs &t, cudaStream_t st, int64_t *launches) {
-  if (t.nlev < 0 || t.nlev > kTmMaxLev || t.KA < 1 || t.w_bytes != 2 * t.KA * kTmWAtom ||
-      t.tile_bytes != 2 * t.KA * tc::kAtomBytes)
+int tree_mma_tile_bytes(int form, int N) { return tm_tile_bytes(form, N); }
+int tree_mma_w_bytes(int form, int N) { return tm_w_bytes(form, N); }
+
+template <int kForm, bool kFull>
+static cudaError_t launch_tm_one(const TreeArgs &u, unsigned nb, size_t smem, cudaStream_t st) {
+  auto kern = k_tree_mma<kTmEpi, kTmSlots, kForm, kFull>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<nb, (kTmEpi + 2) * 32, smem, st>>>(u);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tree_mma(const TreeArgs &t, bool full, cudaStream_t st, int64_t *launches) {
+  if (t.nlev < 0 || t.nlev > kTmMaxLev || t.form < kFormSplit || t.form > kFormFp8 || t.KA != tm_katoms(t.form, t.N) ||
+      t.w_bytes != tm_w_bytes(t.form, t.N) || t.tile_bytes != tm_tile_bytes(t.form, t.N) ||
+      (t.form == kFormFp8 && (!t.ascale || t.k8_steps != (2 * t.N + 31) / 32)) || (full && t.rot != 0) ||
+      (t.rot & 7) != 0)
     return cudaErrorInvalidValue;
   TreeArgs u = t;
-  if (!tm_plan(t.KA, t.nlev, &u.n_abuf, &u.n_sanc)) return cudaErrorInvalidConfiguration;
+  if (!tm_plan(t.form, t.N, t.nlev, &u.n_abuf, &u.n_sanc)) return cudaErrorInvalidConfiguration;
   const size_t smem = tm_smem_bytes(t.w_bytes, t.tile_bytes, u.n_abuf, u.n_sanc);
   const long long nb = (long long)t.n_s * t.n_qb * t.n_tt;
   if (nb <= 0) return cudaSuccess;
   if (nb > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  auto kern = k_tree_mma<kTmEpi, kTmSlots>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  kern<<<(unsigned)nb, (kTmEpi + 2) * 32, smem, st>>>(u);
+  const unsigned g = (unsigned)nb;
+  cudaError_t e;
+  switch (t.form * 2 + (full ? 1 : 0)) {
+    case 0: e = launch_tm_one<kFormSplit, false>(u, g, smem, st); break;
+    case 1: e = launch_tm_one<kFormSplit, true>(u, g, smem, st); break;
+    case 2: e = launch_tm_one<kFormBf16, false>(u, g, smem, st); break;
+    case 3: e = launch_tm_one<kFormBf16, true>(u, g, smem, st); break;
+    case 4: e = launch_tm_one<kFormFp8, false>(u, g, smem, st); break;
+    default: e = launch_tm_one<kFormFp8, true>(u, g, smem, st); break;
+  }
   ++*launches;
-  return cudaGetLastError();
+  return e;
 }
 
 }  // namespace frbx

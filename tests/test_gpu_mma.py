@@ -1,11 +1,13 @@
 """Tensor-core fits (MBD transform as a DFT-GEMM on tcgen05, FP32 accumulation in tensor
-memory) against the FP64 oracle: kernel 3 with BF16 operands (8 significant bits), kernel 5
-with FP8 E4M3 operands (4 significant bits; A scaled per segment by a power of two).  The
-amplitudes are compared with a stated error budget per precision instead of the FP32 path's
-1e-4:
+memory) against the FP64 oracle in the lower precisions: per segment, kernel 3 with BF16
+operands (8 significant bits) and kernel 5 with FP8 E4M3 operands (4 significant bits; A scaled
+per segment by a power of two); in the window tree, kernel 7 (one BF16 product per AP) and
+kernel 8 (E4M3, A scaled per AP).  The amplitudes are compared with a stated error budget per
+precision instead of the FP32 path's 1e-4:
   * |G| at the reported cell: relative error <= max per segment, median <= median;
   * reported cell: its oracle |G| is within `cell` of the oracle maximum;
-  * detections: every oracle crossing with P >= 7 is also a crossing of the search.
+  * detections, both ways: every oracle crossing with P >= 7 is a crossing of the search, and
+    every crossing of the search with P >= 7 is a crossing of the oracle.
 """
 import numpy as np
 import pytest
@@ -20,7 +22,9 @@ pytestmark = pytest.mark.gpu
 # measured on GB300 (vgos / small segments and searches): bf16 max 3.9e-3, median 6.6e-4,
 # cell 1.4e-3; fp8 max 5.6e-2, median 8.2e-3, cell 3.9e-2.  Budgets are about twice those.
 BUDGET = {3: dict(name="bf16", max=1e-2, median=2e-3, cell=1e-2),
-          5: dict(name="fp8", max=1e-1, median=2e-2, cell=8e-2)}
+          5: dict(name="fp8", max=1e-1, median=2e-2, cell=8e-2),
+          7: dict(name="tree bf16", max=1e-2, median=2e-3, cell=1e-2),
+          8: dict(name="tree fp8", max=1e-1, median=2e-2, cell=8e-2)}
 
 
 @pytest.fixture(scope="module")
@@ -69,11 +73,14 @@ def test_mma_fit_segments_vs_oracle(frbx, maker, kernel):
     assert np.all(np.abs(gpu32["amp"] - gpu["amp"]) <= BUDGET[kernel]["max"] * gpu32["amp"])
 
 
-@pytest.mark.parametrize("kernel", [3, 5])
+@pytest.mark.parametrize("kernel", [3, 5, 7, 8])
 @pytest.mark.parametrize("maker", ["vgos", "small"])
 def test_mma_search_detections(frbx, maker, kernel):
-    """Whole search with a tensor-core fit: series within the budget, strong crossings all found."""
+    """Whole search with a tensor-core fit: series within the budget, detections at P >= 7
+    identical both ways."""
     bud = BUDGET[kernel]
+    if maker == "small" and kernel in (7, 8):
+        pytest.skip("the tensor-core window tree needs Ls = 128 (the small setup has Ls = 64)")
     if maker == "vgos":
         wl = synth.make_vgos(T=1500, n_bl=2, n_dm=4)
         wl.dms = np.array([0.0, 200.0, 400.0, 900.0])
@@ -94,8 +101,13 @@ def test_mma_search_detections(frbx, maker, kernel):
     print(f"search {bud['name']} amp rel err: max {rel.max():.2e} median {np.median(rel):.2e}")
     assert rel.max() <= bud["max"] and np.median(rel) <= bud["median"]
     g = {(int(e["series"]), int(e["dm_idx"]), int(e["win_idx"]), int(e["k0"])) for e in out["events"]}
+    o = {(s, d, c.w, c.k0) for (s, d), lst in res.events.items() for c in lst}
     strong = [(s, d, c.w, c.k0) for (s, d), lst in res.events.items() for c in lst if c.p >= 7.0]
+    g_strong = [(int(e["series"]), int(e["dm_idx"]), int(e["win_idx"]), int(e["k0"])) for e in out["events"]
+                if e["pnorm"] >= 7.0]
+    print(f"search {bud['name']}: {len(strong)} oracle and {len(g_strong)} GPU crossings at P >= 7")
     assert strong and all(k in g for k in strong)
+    assert all(k in o for k in g_strong)
 
 
 @pytest.mark.parametrize("kernel", [3, 5])

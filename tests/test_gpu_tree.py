@@ -100,16 +100,21 @@ def test_tree_single_column_class_grid(frbx):
     assert (h.Ls, h.Lm) == (64, 32)
 
 
-def test_tree_delay_windows(frbx):
-    """SBD / MBD search windows: blocks of SBD rows outside the window are skipped, cells
-    outside it are excluded from the maximum."""
+@pytest.mark.parametrize("kernel", [4, 6])
+@pytest.mark.parametrize("sbd,mbd", [((-100.0, 150.0), (-2.0, 3.0)), ((-64.0, 64.0), None),
+                                     ((40.0, 300.0), (10.0, 12.5)), (None, (-1.0, 30.0))])
+def test_tree_delay_windows(frbx, kernel, sbd, mbd):
+    """SBD / MBD search windows: rows and cells outside them are excluded from the maximum.
+    Kernel 4 skips blocks of SBD rows; kernel 6 rotates the SBD rows of its A tiles so the
+    searched ones come first (windows wrapping around row 0 or not, starting off a multiple of
+    8), masks cells of partly searched MBD column blocks and skips the others."""
     wl = _vgos(T=600, n_bl=2, dms=(0.0, 400.0))
     wl.windows = [1, 2, 4, 8]
     st = R.setup_from_workload(wl)
     vis = synth.generate(wl)
-    sbd, mbd = (-100.0, 150.0), (-2.0, 3.0)
     h = frbx.Handle.from_workload(wl)
-    out = h.search(to_dev(vis), wl.dms, wl.windows, want_series=True, kernel=4, sbd_win_ns=sbd, mbd_win_ns=mbd)
+    out = h.search(to_dev(vis), wl.dms, wl.windows, want_series=True, kernel=kernel, sbd_win_ns=sbd, mbd_win_ns=mbd)
+    assert h.stage_times()["tree_tensor"] == (1 if kernel == 6 else 0)
     dk = R.shift_table(st, wl.dms)
     segs, idx, _ = R.all_segments(wl.T, wl.n_bl, wl.windows, dk.max(axis=1))
     am, aq = R.window_masks(st, sbd, mbd)
@@ -135,10 +140,6 @@ def test_tree_rejects_other_windows(frbx):
         with pytest.raises(frbx.FrbxError) as e:
             h.search(to_dev(synth.generate(wl)), wl.dms, [3, 6], kernel=k)
         assert e.value.code == frbx.FRBX_EUNSUPPORTED
-    # the tensor-core tree searches the whole grid only
-    with pytest.raises(frbx.FrbxError) as e:
-        h.search(to_dev(synth.generate(wl)), wl.dms, [1, 2], kernel=6, sbd_win_ns=(-50.0, 50.0))
-    assert e.value.code == frbx.FRBX_EUNSUPPORTED
     # the automatic choice falls back to the per-segment fit for such windows
     out = h.search(to_dev(synth.generate(wl)), wl.dms, [3, 6], want_series=True)
     assert (out["series"]["amp"] >= 0).any()
