@@ -83,8 +83,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel", type=int, default=0)
     ap.add_argument("--no-variants", action="store_true", help="skip the tensor-core and batched variants")
-    ap.add_argument("--batch-bl", type=int, default=3, help="baselines per scan of the batched variant")
-    ap.add_argument("--batch-scale", type=float, default=0.25, help="scan-length factor of the batched variant")
+    ap.add_argument("--batch-bl", type=int, default=45, help="baselines per scan of the batched variant (config 3: 45)")
+    ap.add_argument("--batch-scale", type=float, default=1.0, help="scan-length factor of the batched variant (config 3: 1)")
     ap.add_argument("--batch-steps", type=int, default=2)
     ap.add_argument("--variant-steps", type=int, default=2, help="timed steps of each variant")
     return ap.parse_args()
@@ -114,44 +114,64 @@ def workload_config(name, wl):
             "windows": wl.windows, "l2_flush": "inputs larger than L2 (cube %.2f GB)" % (wl.n_bl * wl.T * wl.C * 8 / 1e9)}
 
 
-def run_batch_variant(frbx, torch, stream, n_bl, t_scale, steps, barrier):
-    """The batched search (many scans, uneven lengths, three setups) through frbx_search_batch:
-    one untimed call (time-tile tuning and graph capture), then `steps` timed calls that
-    replay the captured fit."""
+def run_batch_variant(frbx, torch, stream, n_bl, t_scale, steps, barrier, cpu_seconds=0.0):
+    """The batched search (config 3: many scans of uneven length on three setups) through
+    frbx_search_batch.  At full size (n_bl 45, t_scale 1: 131 GB of cube, made on the GPU by
+    synth.generate_device) one call is timed: it includes the time-tile tuning and the graph
+    capture of the fit (well under 1 % of the call).  Scaled down, one untimed call tunes and
+    captures, then `steps` timed calls replay the captured fit."""
     wls = synth.make_batch(n_bl=n_bl, t_scale=t_scale)
+    full = n_bl == 45 and t_scale == 1.0
     handles, scans = {}, []
     for wl in wls:
         if wl.name not in handles:
             handles[wl.name] = frbx.Handle.from_workload(wl)
-        scans.append((handles[wl.name], torch.from_numpy(synth.generate(wl)).cuda()))
+        vis = synth.generate_device(wl) if full else torch.from_numpy(synth.generate(wl)).cuda()
+        scans.append((handles[wl.name], vis))
+    torch.cuda.synchronize()
     dms, windows = wls[0].dms, wls[0].windows
     cells = sum(float(wl.n_bl) * len(wl.dms) * wl.T * wl.C for wl in wls)
     with frbx.Batch() as b:
-        b.search(scans, dms, windows, stream=stream)
+        if not full:
+            b.search(scans, dms, windows, stream=stream)
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         fit, launches = [], 0
+        n_steps = 1 if full else steps
         e0.record(stream)
-        for _ in range(steps):
+        for _ in range(n_steps):
             outs = b.search(scans, dms, windows, stream=stream)
             info = b.info()
             fit.append(info["fit_ms"])
             launches += info["launches"]
         e1.record(stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / steps
+        ms = e0.elapsed_time(e1) / n_steps
     kinds = {}
     for wl in wls:
         kinds[wl.name] = kinds.get(wl.name, 0) + 1
-    return {"value": cells / (ms / 1e3), "unit": "cells/s", "ms_per_step": ms, "steps": steps,
-            "fit_ms": statistics.mean(fit), "gpu_launches": launches,
-            "workload": f"{len(wls)} scans x {n_bl} baselines, T {min(w.T for w in wls)}..{max(w.T for w in wls)} APs "
-                        f"(1-30 s x {t_scale} at 1 ms), setups {kinds}, {len(dms)} DM trials 0..1500, "
-                        f"windows {windows}",
-            "cube_gb": sum(w.n_bl * w.T * w.C * 8 for w in wls) / 1e9, "cells": cells,
-            "time_tile": info["time_tile"], "graph_captures": info["graph_captures"],
-            "graph_replays": info["graph_replays"],
-            "pulses": int(sum(o["counts"]["pulses"] for o in outs)), "dtype": "f32"}
+    res = {"value": cells / (ms / 1e3), "unit": "cells/s", "ms_per_step": ms, "steps": n_steps,
+           "warmup": 0 if full else 1, "fit_ms": statistics.mean(fit), "gpu_launches": launches,
+           "workload": f"config 3{'' if full else ' scaled'}: {len(wls)} scans x {n_bl} baselines, "
+                       f"T {min(w.T for w in wls)}..{max(w.T for w in wls)} APs (1-30 s x {t_scale} at 1 ms), "
+                       f"setups {kinds}, {len(dms)} DM trials 0..1500, windows {windows}",
+           "data": "synthetic, made on the GPU (synth.generate_device)" if full else "synthetic (synth.generate)",
+           "cube_gb": sum(w.n_bl * w.T * w.C * 8 for w in wls) / 1e9, "cells": cells,
+           "time_tile": info["time_tile"], "graph_captures": info["graph_captures"],
+           "graph_replays": info["graph_replays"],
+           "pulses": int(sum(o["counts"]["pulses"] for o in outs)), "dtype": "f32 (bf16x3 split tensor-core MBD "
+                                                                              "transform on the 1024/2048-point setups)"}
+    if cpu_seconds > 0:
+        # the oracle on a bounded sample of the same data: baseline 0 of the first 2048-point scan
+        i0 = next(i for i, w in enumerate(wls) if w.name == "c2048")
+        wl0 = wls[i0]
+        vis0 = scans[i0][1][0].cpu().numpy()
+        v, cores, desc, _ = run_oracle_sample(wl0, vis0, cpu_seconds)
+        res["cpu_baseline"] = {"value": v, "unit": "cells/s", "cores": cores, "kind": "oracle",
+                               "sample": f"scan {i0} (2048 points, T {wl0.T}): " + desc}
+    del scans, outs
+    torch.cuda.empty_cache()
+    return res
 
 
 def cells_of(wl):
@@ -546,9 +566,15 @@ def main():
         except Exception as exc:
             line_variants["config1_small"] = {"unavailable": str(exc)}
     if not args.no_variants and args.kernel == 0:
+        # config 3 needs the device memory the main workload holds: release it first
+        h.close()
+        del vis_dev
+        torch.cuda.empty_cache()
         try:
             line_variants["batch"] = run_batch_variant(frbx, torch, stream, args.batch_bl, args.batch_scale,
-                                                       max(1, args.batch_steps), barrier)
+                                                       max(1, args.batch_steps), barrier,
+                                                       cpu_seconds=0.0 if (args.no_cpu_baseline or world > 1) else
+                                                       args.cpu_seconds)
         except Exception as exc:
             line_variants["batch"] = {"unavailable": str(exc)}
     if line_variants:

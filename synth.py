@@ -208,6 +208,48 @@ def generate(wl: Workload) -> np.ndarray:
     return out
 
 
+def generate_device(wl: Workload, device="cuda"):
+    """The same recipe as generate() made on the GPU with torch's seeded generator (a different
+    random stream from numpy's PCG64, so the values differ from generate()'s): circular complex
+    Gaussian noise with E|z|^2 = 1, extra noise at rfi_power on the RFI points, boxcar pulses with
+    the physical dispersion delay and the baseline's geometric phase and fringe rate.  For
+    workloads too large to make on the host in reasonable time (the batched workload at full
+    size); returns a complex64 CUDA tensor [n_bl][T][N*J]."""
+    import torch
+    g = torch.Generator(device=device)
+    out = torch.empty((wl.n_bl, wl.T, wl.C), dtype=torch.complex64, device=device)
+    f = wl.point_freqs()
+    cols = (np.array(sorted({n * wl.n_point + j for (n, j) in wl.rfi_points}), dtype=np.int64)
+            if wl.rfi_points else np.zeros(0, np.int64))
+    cols_t = torch.from_numpy(cols).to(device)
+    for b in range(wl.n_bl):
+        g.manual_seed(seed_for(wl.workload_id, "noise", b))
+        torch.view_as_real(out[b]).normal_(0.0, math.sqrt(0.5), generator=g)
+        if cols.size:
+            g.manual_seed(seed_for(wl.workload_id, "rfi", 10 + b))
+            extra = torch.empty((wl.T, cols.size, 2), dtype=torch.float32, device=device)
+            extra.normal_(0.0, math.sqrt(0.5 * wl.rfi_power), generator=g)
+            out[b][:, cols_t] += torch.view_as_complex(extra)
+        if wl.pulses:
+            f_top = float(f.max())
+            m_used = used_points(wl)
+            for p in wl.pulses:
+                a = p.snr / math.sqrt(p.width * m_used)
+                delay_ms = K_DM_PHYS * p.dm * (f ** -2 - f_top ** -2)
+                start = p.t0_bin + np.rint(delay_ms / wl.t_ap_ms).astype(np.int64)
+                ks = (start[:, None] + np.arange(p.width)[None, :]).reshape(-1)
+                cs = np.repeat(np.arange(wl.C), p.width)
+                ok = (ks >= 0) & (ks < wl.T)
+                ks, cs = ks[ok], cs[ok]
+                t_k = ks * wl.t_ap_ms * 1e-3
+                phase = (2 * math.pi * (f[cs] - wl.f0_mhz[0]) * wl.tau_g_ns[b] * 1e-3
+                         + 2 * math.pi * wl.rate_mhz[b] * 1e-3 * (f[cs] / wl.f0_mhz[0]) * t_k + wl.phase0[b])
+                val = torch.from_numpy((a * np.exp(1j * phase)).astype(np.complex64)).to(device)
+                out[b].index_put_((torch.from_numpy(ks).to(device), torch.from_numpy(cs).to(device)), val,
+                                  accumulate=True)
+    return out
+
+
 def pure_tone_segment(wl: Workload, tau_ns: float, amp: float = 1.0) -> np.ndarray:
     """Noise-free [N*J] spectrum a*exp(2 pi i (f - f0[0]) tau) for transform pins."""
     f = wl.point_freqs()
