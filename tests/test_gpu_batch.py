@@ -100,11 +100,12 @@ def test_batch_equals_per_scan_search(frbx, kernel):
         _same(o, h.search(v, DMS, windows, **kw))
 
 
-@pytest.mark.parametrize("kernel", [4, 6])
-def test_batch_window_tree_only(frbx, kernel):
+@pytest.mark.parametrize("kernel,sbd,mbd", [(4, None, None), (6, None, None), (6, (-64.0, 64.0), None),
+                                            (6, (40.0, 300.0), (10.0, 12.5)), (4, (40.0, 300.0), (10.0, 12.5))])
+def test_batch_window_tree_only(frbx, kernel, sbd, mbd):
     """Window-tree kernels (4: CUDA cores, 6: tensor cores) on VGOS-like scans of three
-    lengths, one spanning several time tiles, against frbx_search with the same kernel;
-    replay with new data."""
+    lengths, one spanning several time tiles, against frbx_search with the same kernel, on the
+    whole grid and with delay search windows; replay with new data."""
     wls = []
     for T, off in ((2300, 0), (700, 5), (1200, 9)):
         wl = synth.make_vgos(T=T, n_bl=2, n_dm=len(DMS), seed_offset=off)
@@ -115,7 +116,7 @@ def test_batch_window_tree_only(frbx, kernel):
         wls.append(wl)
     h = frbx.Handle.from_workload(wls[0])
     vis = [to_dev(synth.generate(wl)) for wl in wls]
-    kw = dict(combos=[0b11], want_series=True, want_events=True, kernel=kernel)
+    kw = dict(combos=[0b11], want_series=True, want_events=True, kernel=kernel, sbd_win_ns=sbd, mbd_win_ns=mbd)
     with frbx.Batch() as b:
         out = b.search([(h, v) for v in vis], DMS, [1, 2, 4, 8, 16], **kw)
         vis[0].mul_(0.5)  # same buffers, new data: the captured graph is replayed
