@@ -474,8 +474,9 @@ def main():
     #    per AP, kernel 8: E4M3), pulses compared with the default path's;
     #  * the windowed regime: the same workload with a +-64 ns SBD search window (9 of 128 SBD
     #    rows) and the whole MBD range, where the metric's 8 B/cell HBM fraction applies;
-    #  * config 1 (the small S-band cube, plain) and config 4 (the same cube with the MBD
-    #    transform as a BF16 / E4M3 DFT-GEMM per segment, kernels 3 and 5).
+    #  * config 1 (the small S-band cube, plain: the automatic choice, the FP32 window tree, and
+    #    the per-segment direct fit) and config 4 (the same cube with the MBD transform as a
+    #    BF16 / E4M3 DFT-GEMM per segment, kernels 3 and 5).
     line_variants = {}
 
     def timed(hh, vis, wll, cmb, kernel, steps, **kw):
@@ -547,13 +548,16 @@ def main():
             scells = cells_of(ws)
             base = None
             for vname, vk, vdt in (("config1_small", 0, "f32"),
+                                   ("config1_small_direct", 1, "f32"),
                                    ("config4_bf16", 3, "bf16 operands, f32 accumulate (MBD DFT-GEMM per segment)"),
                                    ("config4_fp8", 5, "e4m3 operands (A scaled per segment), f32 accumulate "
                                                       "(MBD DFT-GEMM per segment)")):
                 vms, vfit, _, o5 = timed(hs, svis, ws, wcombos, vk, max(3, args.variant_steps))
                 ent = {"value": world * scells / (vms / 1e3), "unit": "cells/s", "ms_per_step": vms, "fit_ms": vfit,
                        "dtype": vdt, "workload": workload_config("small", ws)["workload"],
-                       "pulses": int(o5["counts"]["pulses"]), "groups": int(o5["counts"]["groups"])}
+                       "pulses": int(o5["counts"]["pulses"]), "groups": int(o5["counts"]["groups"]),
+                       "fit": ("FP32 window tree (kernel 4)" if hs.stage_times()["tree_chunks"] > 0 else
+                               f"per-segment fit (kernel {vk})")}
                 if base is None:
                     base = o5
                 else:

@@ -94,7 +94,8 @@ typedef struct frbx_setup {
  *                3 = per-segment BF16 tensor-core DFT-GEMM (about 4e-3 relative error;
  *                    Ls 64 or 128, whole grid);
  *                4 = window tree: power-of-two windows built from one-AP matrices by the
- *                    additivity of Sec. 5.1, FP32 on the CUDA cores (windows <= 64 APs);
+ *                    additivity of Sec. 5.1, FP32 on the CUDA cores (windows <= 64 APs;
+ *                    Ls a multiple of 32, Lm 16 or a multiple of 32);
  *                5 = as 3 with FP8 E4M3 operands (about 6e-2 relative error);
  *                6 = window tree with the MBD transform as a three-term split-BF16
  *                    tensor-core GEMM, FP32 accumulation (about 1e-5 relative; Ls 128,

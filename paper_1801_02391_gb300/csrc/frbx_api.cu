@@ -283,6 +283,11 @@ int frbx_create(const frbx_setup *s, frbx_handle **out) {
     for (int g2 = 0; g2 < 32; ++g2)
       for (int o = 0; o < 4; ++o)
         h->slot_n[g2][o] = (short)(o < (int)res[(size_t)g2].size() ? res[(size_t)g2][(size_t)o] : -1);
+  }
+  if (h->Ls % 32 == 0 && (h->Lm % 32 == 0 || h->Lm == 16)) {
+    // Lm = 16: the tree uses the h = 0 half alone (one thread per row, all 16 cells), whose
+    // twiddles below are 1 (q1 = 0)
+    const int PM = std::max(1, h->Lm / 32);
     // window-tree fit: channel n sits in slot (g_n mod 16) + 16 o of a Y row (o its rank in
     // the class); half h of the 32-point DIF over residues g2 = g_n mod 32 takes it with
     // exp(-2 pi i [(g_n q1 mod Lm) / Lm + h (g_n mod 32) / 32]) -- the MBD twiddle times the
@@ -733,8 +738,9 @@ void plan_tree(const frbx_handle *h, const FitArgs &a, int nlev, const int32_t *
   t.slot_of = h->d_tree_slot;
   t.Ls = h->Ls;
   t.Lm = h->Lm;
-  t.PM = h->Lm / 32;
-  t.RB = 128 / (2 * t.PM);
+  t.PM = std::max(1, h->Lm / 32);
+  t.half = h->Lm == 16;
+  t.RB = frbx::tree_rows_per_block(h->Ls, h->Lm);
   t.n_mb = h->Ls / t.RB;
   t.nlev = nlev;
   for (int &e : t.emit_w) e = -1;
@@ -1160,7 +1166,8 @@ static int search_impl(frbx_handle *h, const void *vis, int32_t vis_on_device, i
   const bool tree_tc = tree_tc_shape && frbx::tree_mma_fits(tc_form, h->N, nlev);
   if ((p.kernel == 4 && !tree_ok) || (p.kernel >= 6 && !tree_tc))
     return fail(h, FRBX_EUNSUPPORTED,
-                "window-tree fit needs power-of-two windows <= 64 and Ls, Lm multiples of 32 (tensor cores: Ls 128, "
+                "window-tree fit needs power-of-two windows <= 64, Ls a multiple of 32 and Lm 16 or a multiple of 32 "
+                "(tensor cores: Ls 128, "
                 "2N <= 128, Lm a multiple of 32)");
   if (p.kernel == 4 || p.kernel >= 6 || (p.kernel == 0 && tree_ok)) {
     const int form = p.kernel >= 6 || (p.kernel == 0 && tree_tc) ? tc_form : -1;

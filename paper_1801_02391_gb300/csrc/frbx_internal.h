@@ -160,6 +160,7 @@ struct TreeArgs {
   int n_dm, S_tot;
   const int *win_off;      // [n_win]
   int N, NS, Ls, Lm, PM, RB, n_mb, TT, n_tt, nlev;
+  int half;                // k_tree_mbd with Lm = 16: one thread per SBD row, its 16 cells q = 0..15
   int emit_w[8];           // window index of level e (window 2^e), -1 = not searched
   int m_lo, m_len, q_lo, q_len;
   const int *slot_of;      // [N] slot of channel n in a Y row: (g_n mod 16) + 16 rank
@@ -192,6 +193,7 @@ int tree_mma_tile_bytes(int form, int N);        // one AP's A operand in its sh
 int tree_mma_w_bytes(int form, int N);           // the DFT operand of one block of 32 q
 cudaError_t launch_tree_mma(const TreeArgs &t, bool full, cudaStream_t st, int64_t *launches);
 bool tree_supported(int Ls, int Lm, int N, int J, int s16, const int *windows, int n_win, int *nlev);
+int tree_rows_per_block(int Ls, int Lm);  // SBD rows per k_tree_mbd CTA
 size_t tree_anchor_floats(int nlev);  // float2 per MBD CTA in TreeArgs::anc_g
 cudaError_t launch_tree_sbd(const FitArgs &a, const TreeArgs &t, cudaStream_t st, int64_t *launches);
 cudaError_t launch_tree_mbd(const TreeArgs &t, bool full, cudaStream_t st, int64_t *launches);

@@ -239,16 +239,22 @@ __global__ void __launch_bounds__(kTreeThreads, 3) k_tree_mbd(const __grid_const
   const int tt = item % t.n_tt;
   item /= t.n_tt;
   const int mb = item % t.n_mb, s = item / t.n_mb;
-  const int tpr = 2 * PM;
-  const int rr = tid / tpr, q1 = (tid >> 1) & (PM - 1), h = tid & 1;
+  // a thread owns 16 cells of one row: classes q1 and half h of the 32-point DIF (tpr = 2 PM
+  // threads per row), or with Lm = 16 the whole row (the h = 0 half, q = bitrev4(c)); threads
+  // past the block's RB rows (Lm = 16 and Ls < 128) only take part in the barriers
+  const bool half = t.half != 0;
+  const int tpr = half ? 1 : 2 * PM;
+  const int rr0 = tid / tpr, q1 = half ? 0 : (tid >> 1) & (PM - 1), h = half ? 0 : tid & 1;
+  const bool row_ok = rr0 < RB;
+  const int rr = row_ok ? rr0 : 0;
   const int m = mb * RB + rr;
   const int2 sd = t.series[s];
   const int kd = t.T - t.dk_max[sd.y];
   const int kb = tt * t.TT;
   if (kb >= kd) return;  // every segment starting here runs past the scan
-  bool row_in = true;
+  bool row_in = row_ok;
   if (!kFull) {
-    row_in = ((m - t.m_lo) & (t.Ls - 1)) < t.m_len;
+    row_in = row_ok && ((m - t.m_lo) & (t.Ls - 1)) < t.m_len;
     if (!__syncthreads_or(row_in)) return;  // no SBD row of this block is searched
   }
   const int lmax = 1 << t.nlev;
@@ -259,14 +265,15 @@ __global__ void __launch_bounds__(kTreeThreads, 3) k_tree_mbd(const __grid_const
   for (int i = tid; i < tree_global_anchors(t.nlev) * 16 * kTreeThreads; i += kTreeThreads)
     ancg[i] = make_float2(0.f, 0.f);
   // cells this thread may report: c -> q2 = 2 bitrev4(c) + h, q = q1 + PM q2
-  unsigned cmask = 0xffffu;
+  unsigned cmask = row_ok ? 0xffffu : 0u;
   if (!kFull) {
     cmask = 0u;
     if (row_in) {
 #pragma unroll
       for (int c = 0; c < 16; ++c) {
         const int q2 = 2 * (bitrev5(c) >> 1) + h;
-        if ((((q1 + PM * q2) - t.q_lo) & (Lm - 1)) < t.q_len) cmask |= 1u << c;
+        const int q = half ? q2 >> 1 : q1 + PM * q2;
+        if (((q - t.q_lo) & (Lm - 1)) < t.q_len) cmask |= 1u << c;
       }
     }
   }
@@ -357,7 +364,7 @@ __global__ void __launch_bounds__(kTreeThreads, 3) k_tree_mbd(const __grid_const
             const int L = __ffs(win) - 1, tl = warp * 32 + L;
             const int q2 = 32 - (int)(wmax & 63u);
             const int mm = mb * RB + tl / tpr, qq1 = (tl >> 1) & (PM - 1);
-            r2 = make_uint2(wmax & ~63u, (unsigned)(mm * Lm + qq1 + PM * q2));
+            r2 = make_uint2(wmax & ~63u, (unsigned)(mm * Lm + (half ? q2 >> 1 : qq1 + PM * q2)));
           }
           red[(buf * (kTreeMaxLev + 1) + e) * 4 + warp] = r2;
         }
@@ -429,10 +436,10 @@ __global__ void k_tree_finalize(frbx_seg *series, long long n_el, int S_tot, int
 void set_tree_constants() { upload_w32(); }
 
 bool tree_supported(int Ls, int Lm, int N, int J, int s16, const int *windows, int n_win, int *nlev) {
-  if (Ls % 32 != 0 || Lm % 32 != 0 || J > Ls || s16 < 1 || s16 > 4) return false;
-  const int PM = Lm / 32, NS = 16 * s16;
+  if (Ls % 32 != 0 || (Lm % 32 != 0 && Lm != 16) || J > Ls || s16 < 1 || s16 > 4) return false;
+  const int PM = std::max(1, Lm / 32), NS = 16 * s16;
   if (2 * PM > kTreeThreads || N > NS) return false;
-  const int RB = kTreeThreads / (2 * PM);
+  const int RB = tree_rows_per_block(Ls, Lm);
   if (Ls % RB != 0) return false;
   int lmax = 1;
   for (int w = 0; w < n_win; ++w) {
@@ -447,6 +454,8 @@ bool tree_supported(int Ls, int Lm, int N, int J, int s16, const int *windows, i
   const size_t sbd = sizeof(float2) * ((size_t)Ls * N + (size_t)N * (JP + 1) + (size_t)(Ls / 32) * (JP + 1));
   return tree_smem_bytes(NS, PM, RB, *nlev) <= max_smem_optin() && sbd <= max_smem_optin();
 }
+
+int tree_rows_per_block(int Ls, int Lm) { return Lm == 16 ? std::min(kTreeThreads, Ls) : kTreeThreads / (2 * (Lm / 32)); }
 
 size_t tree_anchor_floats(int nlev) { return (size_t)tree_global_anchors(nlev) * 16 * kTreeThreads; }
 

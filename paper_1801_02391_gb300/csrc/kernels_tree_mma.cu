@@ -13,17 +13,16 @@
 // series and walks a time tile AP by AP (10 warps):
 //   warp 9 (one lane) copies each AP's split A tiles (written by k_tree_sbd in their
 //          shared-memory image) into a ring with cp.async.bulk;
-//   warp 8 allocates tensor memory and one of its lanes issues an AP's MMAs into one of two
-//          accumulator slots of 128 columns, so it runs one AP ahead.  A tcgen05.mma of
-//          M = 128 and K = 16 costs about the same for N = 64 and N = 128, so the two products
-//          of A_hi are one N = 128 MMA against the stacked [W_hi; W_lo], D = [A_hi W_hi |
-//          A_hi W_lo + A_lo W_hi], and the epilogue adds the halves: 2 K/16 MMAs per AP
-//          instead of 3 K/16;
+//   warp 8 allocates tensor memory and runs the MMA loop convergently; one elected lane issues
+//          an AP's MMAs into one of two accumulator slots of 64 columns, so it runs one AP
+//          ahead: per K step three N = 64 MMAs, A_hi W_hi, A_hi W_lo and A_lo W_hi, all
+//          accumulating into the same slot (the issue keeps pace with the tensor pipe, and the
+//          epilogue reads one 64-column result per AP);
 //   warps 0-7 (row quarter w % 4, q half w / 4) read G_1(k) into registers (freeing its slot
 //          at once), keep it there as G_1(k - 1) for the next AP, walk their 16 cells through
-//          the window tree with packed FP32x2 arithmetic (the anchors of levels 2 to 5, the
-//          first halves of windows 4 to 32, in tensor memory after the slots; a level-6
-//          anchor, used every 32 APs, in shared memory), and merge every emitted segment's
+//          the window tree with packed FP32x2 arithmetic (the anchors of levels 2 to 6, the
+//          first halves of windows 4 to 64, in tensor memory after the slots; shared memory
+//          takes anchor levels only where tensor memory has no room), and merge every emitted segment's
 //          warp maximum into the series by a 64-bit atomicMax, as k_tree_mbd does per block:
 //          the warps never wait for one another.
 // Two lower-precision forms of the same tree run one product per AP instead of three: kernel 7
@@ -64,8 +63,9 @@ constexpr int kFormSplit = 0;  // A_hi W_hi + A_hi W_lo + A_lo W_hi in BF16 (FP3
 constexpr int kFormBf16 = 1;   // A_hi W_hi
 constexpr int kFormFp8 = 2;    // E4M3 x E4M3, A scaled per AP
 
-// one accumulator slot: [A_hi W_hi | A_hi W_lo + A_lo W_hi] for the split form, else one product
-__host__ __device__ constexpr int tm_slot_cols(int form) { return form == kFormSplit ? 2 * kTmCols : kTmCols; }
+// one accumulator slot: Re G and Im G of the block's 32 q (the split form's three products
+// accumulate into it)
+__host__ __device__ constexpr int tm_slot_cols(int) { return kTmCols; }
 __host__ __device__ constexpr int tm_tmem_anchors(int form, int slots) {
   return (kTmTmemCols - slots * tm_slot_cols(form)) / kTmCols;
 }
@@ -181,8 +181,7 @@ __device__ __forceinline__ void mma_e4m3(uint32_t d_tmem, uint64_t ad, uint64_t 
 }  // namespace
 
 // kEpi epilogue warps, then the MMA warp and the loader warp.  Tensor memory: kSlots accumulator
-// slots (128 columns for the split form, else 64), then the anchors of levels 2, 3, ... at
-// 64-column steps.  Shared memory: W, the A-tile ring (t.n_abuf deep), then the t.n_sanc deepest
+// slots of 64 columns, then the anchors of levels 2, 3, ... at 64-column steps.  Shared memory: W, the A-tile ring (t.n_abuf deep), then the t.n_sanc deepest
 // anchor levels as [level][16 column quads][128 rows] float4.  kForm: the MBD product (above);
 // kFull: the whole delay grid is searched (no windows, no row rotation).
 template <int kEpi, int kSlots, int kForm, bool kFull>
@@ -287,7 +286,7 @@ __global__ void __launch_bounds__((kEpi + 2) * 32, 1) k_tree_mma(const __grid_co
     // per-instruction moves into uniform registers); one elected lane issues the MMAs and
     // commits, which keeps the issue rate at the tensor pipe's pace.
     const bool leader = tc::elect_one();
-    const uint32_t id64 = idesc_bf16(kTmCols), id128 = idesc_bf16(2 * kTmCols), id8 = idesc_e4m3(kTmCols);
+    const uint32_t id64 = idesc_bf16(kTmCols), id8 = idesc_e4m3(kTmCols);
     // descriptors of the K steps differ only in the start address field (address / 16, in
     // the low 14 bits, which shared-memory offsets below 256 KB never carry out of)
     const uint32_t a_half16 = (uint32_t)(t.KA * tc::kAtomBytes) >> 4;
@@ -307,21 +306,15 @@ __global__ void __launch_bounds__((kEpi + 2) * 32, 1) k_tree_mma(const __grid_co
       const uint32_t d_tmem = tmem + (uint32_t)(slot * kSlotCols);
       if (leader) {
         if constexpr (kForm == kFormSplit) {
-          // D[0:64] = A_hi W_hi, D[64:128] = A_hi W_lo (one N = 128 MMA per K step) + A_lo W_hi
+          // D = A_hi W_hi + A_hi W_lo + A_lo W_hi, all N = 64 into one accumulator
           for (int ka = 0; ka < t.KA; ++ka) {
 #pragma unroll
             for (int k4 = 0; k4 < 4; ++k4) {
               const uint32_t ao = (uint32_t)((ka * tc::kAtomBytes + k4 * 32) >> 4);
               const uint32_t bo = (uint32_t)((ka * 2 * kTmWAtom + k4 * 32) >> 4);
-              mma_bf16(d_tmem, a0 + ao, w0 + bo, id128, (ka | k4) ? 1u : 0u);
-            }
-          }
-          for (int ka = 0; ka < t.KA; ++ka) {
-#pragma unroll
-            for (int k4 = 0; k4 < 4; ++k4) {
-              const uint32_t ao = (uint32_t)((ka * tc::kAtomBytes + k4 * 32) >> 4);
-              const uint32_t bo = (uint32_t)((ka * 2 * kTmWAtom + k4 * 32) >> 4);
-              mma_bf16(d_tmem + (uint32_t)kTmCols, a0 + a_half16 + ao, w0 + bo, id64, 1u);
+              mma_bf16(d_tmem, a0 + ao, w0 + bo, id64, (ka | k4) ? 1u : 0u);
+              mma_bf16(d_tmem, a0 + ao, w0 + bo + (uint32_t)(kTmWAtom >> 4), id64, 1u);
+              mma_bf16(d_tmem, a0 + a_half16 + ao, w0 + bo, id64, 1u);
             }
           }
         } else if constexpr (kForm == kFormBf16) {
@@ -460,14 +453,10 @@ __global__ void __launch_bounds__((kEpi + 2) * 32, 1) k_tree_mma(const __grid_co
       const int k = kb + i;
       if (!__all_sync(0xffffffffu, tc::mbar_wait(&bar_accfull[slot], sph, abortp, t.timeout))) return false;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      uint64_t lre[kP], lim[kP];
       const uint32_t cur = lane_base + (uint32_t)(slot * kSlotCols);
       tm_ld<kQ>(cur + c_re, cre);
       tm_ld<kQ>(cur + c_im, cim);
-      if constexpr (kForm == kFormSplit) {
-        tm_ld<kQ>(cur + kTmCols + c_re, lre);
-        tm_ld<kQ>(cur + kTmCols + c_im, lim);
-      }
+
       float inv_s = 1.f;  // E4M3 form: the AP's A was scaled by s, a power of two
       if constexpr (kForm == kFormFp8) inv_s = __ldg(t.ascale + (size_t)s * t.T + k);
       // levels whose window ends at k, and which of them emit a segment of this time tile
@@ -480,13 +469,7 @@ __global__ void __launch_bounds__((kEpi + 2) * 32, 1) k_tree_mma(const __grid_co
         if (e <= E && woff[e] >= 0 && k0 >= kb && k0 < kb + t.TT) em |= 1u << e;
       }
       tm_wait_ld();
-      if constexpr (kForm == kFormSplit) {
-#pragma unroll
-        for (int p = 0; p < kP; ++p) {
-          cre[p] = add2(cre[p], lre[p]);
-          cim[p] = add2(cim[p], lim[p]);
-        }
-      } else if constexpr (kForm == kFormFp8) {
+      if constexpr (kForm == kFormFp8) {
         const uint64_t iv = pk(__float_as_uint(inv_s), __float_as_uint(inv_s));
 #pragma unroll
         for (int p = 0; p < kP; ++p) {

@@ -3,7 +3,7 @@ matrices by the additivity of Sec. 5.1, G_{k0,l} + G_{k0+l,l} = G_{k0,2l}.  Kern
 MBD transform on the CUDA cores in FP32; kernel 6 (the automatic choice where it applies)
 runs it on the tensor cores as a three-term split-BF16 GEMM with FP32 accumulation (about
 1e-5 relative).  Both are compared with the FP64 oracle element by element, to the FP32
-tolerance, on several grid shapes (Lm/32 = 16, 8 and 1 MBD column classes), window sets with
+tolerance, on several grid shapes (Lm/32 = 16, 8 and 1 MBD column classes, and Lm = 16), window sets with
 and without gaps, more than one time tile, delay windows and scans that DM trials sweep past."""
 import numpy as np
 import pytest
@@ -98,6 +98,48 @@ def test_tree_single_column_class_grid(frbx):
                          f0=800.0 + 16.0 * np.array([0, 3, 7, 12]))
     h, _ = _run(frbx, wl, [1, 2, 4, 8])
     assert (h.Ls, h.Lm) == (64, 32)
+
+
+@pytest.mark.parametrize("windows", [[2, 4, 8, 16], [1, 2, 4, 8, 16, 32, 64], [4]])
+def test_tree_sixteen_cell_mbd(frbx, windows):
+    """The S-band setup (8 channels x 32 points at 32 MHz spacing): Lm = 16, so one thread holds
+    a whole SBD row (16 MBD cells, the even half of the 32-point structure) and 64 rows fill
+    half a block.  The automatic choice is this tree; it matches the oracle element by element
+    and agrees with the per-segment direct fit (kernel 1)."""
+    wl = synth.make_small(T=1400, dms=np.arange(530.0, 591.0, 20.0))
+    h, out = _run(frbx, wl, windows, combos=(7, 3))
+    assert (h.Ls, h.Lm) == (64, 16)
+    vis = to_dev(synth.generate(wl))
+    auto = h.search(vis, wl.dms, windows, want_series=True)
+    assert h.stage_times()["tree_chunks"] > 0 and h.stage_times()["tree_tensor"] == 0
+    assert np.array_equal(auto["series"], out["series"])
+    seg = h.search(vis, wl.dms, windows, want_series=True, kernel=1)
+    ok = seg["series"]["amp"] >= 0
+    assert np.array_equal(ok, out["series"]["amp"] >= 0)
+    rel = np.abs(out["series"]["amp"][ok] - seg["series"]["amp"][ok]) / seg["series"]["amp"][ok]
+    assert rel.max() <= 1e-4
+
+
+@pytest.mark.parametrize("sbd,mbd", [(None, None), ((-100.0, 150.0), (-10.0, 12.0)), ((300.0, 900.0), (5.0, 20.0))])
+def test_tree_sixteen_cell_mbd_full_block(frbx, sbd, mbd):
+    """8 channels x 64 points: Ls = 128 and Lm = 16, every thread of the block a row; with and
+    without SBD / MBD search windows (a window wrapping around zero delay and one that skips
+    the first SBD rows)."""
+    wl = synth.make_tiny(n_chan=8, n_point=64, T=900, n_bl=2, dms=(0.0, 20.0, 60.0), windows=(1, 2, 4, 8),
+                         f0=1400.0 + 32.0 * np.arange(8))
+    st = R.setup_from_workload(wl)
+    assert (st.Ls, st.Lm) == (128, 16)
+    vis = synth.generate(wl)
+    h = frbx.Handle.from_workload(wl)
+    out = h.search(to_dev(vis), wl.dms, wl.windows, want_series=True, kernel=4, sbd_win_ns=sbd, mbd_win_ns=mbd)
+    dk = R.shift_table(st, wl.dms)
+    segs, idx, _ = R.all_segments(wl.T, wl.n_bl, wl.windows, dk.max(axis=1))
+    am, aq = R.window_masks(st, sbd, mbd)
+    ref = R.fit_segments(st, vis, dk, segs, am, aq)
+    flat = out["series"].reshape(-1)[idx]
+    assert (flat["amp"] >= 0).all()
+    assert_fit_match(st, vis, dk, segs, flat, ref, (am, aq))
+    assert am[flat["sbd_idx"].astype(int)].all() and aq[flat["mbd_idx"].astype(int)].all()
 
 
 @pytest.mark.parametrize("kernel", [4, 6])
