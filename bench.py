@@ -77,7 +77,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="frbx", choices=["frbx", "reference"])
-    ap.add_argument("--workload", default="vgos", choices=["vgos", "small", "vgos-slice", "vgos-profile"])
+    ap.add_argument("--workload", default="vgos", choices=["vgos", "small", "vgos-slice", "vgos-profile", "vgos-dm8"])
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -96,6 +96,10 @@ def make_workload(name):
         combos = [(1 << wl.n_bl) - 1]
     elif name == "vgos-profile":  # one baseline of the VGOS cube (328 MB > L2), 4 DM trials
         wl = synth.make_vgos(n_bl=1, n_dm=4)
+        combos = [1]
+    elif name == "vgos-dm8":     # one baseline, 8 neighbouring DM trials of the 512-trial grid (as
+        wl = synth.make_vgos(T=10000, n_bl=1, n_dm=512)  # within a chunk), cube 164 MB > L2
+        wl.dms = wl.dms[256:264].copy()
         combos = [1]
     elif name == "vgos-slice":   # small case of the same kernel, for profiler captures
         wl = synth.make_vgos(T=2400, n_bl=1, n_dm=8)

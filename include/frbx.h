@@ -407,9 +407,12 @@ int frbx_calibrate(frbx_handle *h, const void *vis, int32_t vis_on_device, int32
  * The device work of the fit -- the dominant stage -- is one persistent launch per setup (and
  * per distinct window layout), whose CTAs claim (scan, baseline, time tile, DM trial) work
  * items from a device counter, so uneven scans load-balance; these launches are captured once
- * into a CUDA graph and replayed while the scans' shapes and buffers stay the same.  The time
- * tile of each setup is chosen by timing candidates (32, 64, 128 APs) on a sample of its
- * items the first time a setup shape is seen by the batch object.
+ * into a CUDA graph and replayed while the scans' shapes and buffers stay the same; setups
+ * that take the window-tree fit add its two passes per chunk of series to the graph.  The time
+ * tile of each setup is chosen by timing candidates on a sample the first time a setup shape
+ * is seen by the batch object: 32, 64, 128 APs for the per-segment fit (a stretch of its work
+ * items), 512, 1024, 2048 APs for the window tree (one chunk of the setup's longest scan).
+ * The window tree's results do not depend on its tile.
  * Normalisation, threshold and extraction then run per scan as in frbx_search.
  */
 typedef struct frbx_batch frbx_batch;

@@ -707,6 +707,11 @@ int run_stats(frbx_handle *h, StatsArgs sa, cudaStream_t st, std::vector<frbx_ev
 // builds every window from them and merges the maxima into the series buffer (as 64-bit
 // keys, zeroed first); a last pass turns the keys into frbx_seg records.  d_tab holds the
 // window tables and valid-segment counts in the layout frbx_search uploads.
+// Time tile of the window-tree fit (APs per MBD CTA, a multiple of 64); frbx_search_batch
+// measures the candidates per setup.
+constexpr int kTreeTT = 1024;
+constexpr int kTreeTuneTT[] = {512, 1024, 2048};
+
 struct TreeRun {
   frbx::TreeArgs t{};
   bool full = true;
@@ -722,7 +727,7 @@ struct TreeRun {
 // 1 BF16, 2 E4M3).
 void plan_tree(const frbx_handle *h, const FitArgs &a, int nlev, const int32_t *windows, int n_win,
                const std::vector<int> &dkm, int n_bl, int T, int n_dm, const int *win_off, int S_tot, size_t budget,
-               int form, TreeRun *r) {
+               int form, TreeRun *r, int TT = kTreeTT) {
   const bool mma = form >= 0;
   frbx::TreeArgs &t = r->t;
   t = frbx::TreeArgs{};
@@ -750,7 +755,7 @@ void plan_tree(const frbx_handle *h, const FitArgs &a, int nlev, const int32_t *
   t.q_lo = a.q_lo;
   t.q_len = a.q_len;
   t.tw = h->d_tree_tw;
-  t.TT = 1024;
+  t.TT = TT;
   t.n_tt = (T + t.TT - 1) / t.TT;
   t.k_per_cta = 16;
   t.n_ktile = (T + t.k_per_cta - 1) / t.k_per_cta;
@@ -766,13 +771,19 @@ void plan_tree(const frbx_handle *h, const FitArgs &a, int nlev, const int32_t *
     t.w_bytes = frbx::tree_mma_w_bytes(form, h->N);
     // delay windows: rotate the SBD rows so the searched ones come first (in groups of 8)
     t.rot = r->full ? 0 : (a.m_lo & ~7);
+    // rows searched after the rotation: [m_lo mod 8, m_lo mod 8 + m_len) in 32-row quarters
+    const int nq = r->full ? 4 : ((a.m_lo & 7) + a.m_len + 31) / 32;
+    t.pack = nq == 1 ? 4 : nq == 2 ? 2 : 1;
+    t.prow = 128 / t.pack;
+    t.piece_bytes = t.tile_bytes / t.pack;
+    t.n_tg = (t.n_tt + t.pack - 1) / t.pack;
     t.n_qb = h->Lm / 32;
     t.log2Lm = a.log2Lm;
     t.err = (int *)h->errflag.p;
     t.timeout = wait_cycles(h);
     t.drain_timeout = kDrainCycles;
     t.hold = h->lim.hold_producers ? 1 : 0;
-    t.yt_series = (size_t)T * t.tile_bytes;
+    t.yt_series = (size_t)T * t.piece_bytes;
     t.y_series = t.yt_series / sizeof(float2);
   }
   r->ser.clear();
@@ -1659,8 +1670,8 @@ extern "C" int frbx_search_batch(frbx_batch *b, const frbx_scan *scans, int32_t 
   std::vector<frbx::BatchScan> desc;
   for (size_t g = 0; g < setups.size(); ++g) {
     frbx_handle *h = setups[g];
-    if (tree_lev[g] >= 0) {  // the window-tree fit has its own fixed tiling
-      b->last_tt[g] = 1024;
+    if (tree_lev[g] >= 0) {  // the window tree's time tile is measured with its own passes below
+      b->last_tt[g] = kTreeTT;
       continue;
     }
     std::string tkey = std::to_string(h->N) + "x" + std::to_string(h->J) + "/" + std::to_string(h->Ls) + "/" +
@@ -1731,23 +1742,86 @@ extern "C" int frbx_search_batch(frbx_batch *b, const frbx_scan *scans, int32_t 
       if (tree_lev[g] >= 0) FRBX_BCK(b, ensure(setups[g], setups[g]->errflag, sizeof(int)));
     size_t free_b = 0, total_b = 0;
     FRBX_BCK(b, cudaMemGetInfo(&free_b, &total_b));
-    for (int i = 0; i < n_scans; ++i) {
+    auto tree_budget = [&](const frbx_handle *h) {
+      return h->lim.tree_chunk_bytes > 0
+                 ? (size_t)h->lim.tree_chunk_bytes
+                 : std::min<size_t>((size_t)16 << 30, (free_b + h->ytree.bytes) / (4 * n_tree_setups));
+    };
+    auto tree_args = [&](int i) {
       const int g = plan[(size_t)i].setup;
-      if (tree_lev[(size_t)g] < 0) continue;
-      frbx_handle *h = setups[(size_t)g];
-      const size_t budget =
-          h->lim.tree_chunk_bytes > 0
-              ? (size_t)h->lim.tree_chunk_bytes
-              : std::min<size_t>((size_t)16 << 30, (free_b + h->ytree.bytes) / (4 * n_tree_setups));
       FitArgs a = fit_args(g, 1024);
-      fill_fit_tables(h, &a, (const float2 *)scans[i].vis_dev, scans[i].T, n_dm);
+      fill_fit_tables(setups[(size_t)g], &a, (const float2 *)scans[i].vis_dev, scans[i].T, n_dm);
       a.win_off = d_tab + woff_at[(size_t)i];
       a.n_valid = d_tab + plan[(size_t)i].nval_off;
       a.S_tot = plan[(size_t)i].L.S_tot;
       a.out = d_series + plan[(size_t)i].series_off;
+      return a;
+    };
+    // the window tree's time tile per setup: measured once per (setup shape, DM count, windows,
+    // form, delay window) on one chunk of the series of the setup's longest scan, twice per
+    // candidate; the faster minimum wins (the real fit below rewrites that scan's series)
+    for (size_t g = 0; g < setups.size(); ++g) {
+      if (tree_lev[g] < 0) continue;
+      frbx_handle *h = setups[g];
+      std::string tkey = "tree/" + std::to_string(h->N) + "x" + std::to_string(h->J) + "/" + std::to_string(h->Ls) +
+                         "/" + std::to_string(h->Lm) + "/" + std::to_string(n_dm) + "/" + std::to_string(tree_tc[g]);
+      for (int w = 0; w < n_win; ++w) tkey += "," + std::to_string(windows[w]);
+      tkey += "/" + std::to_string(fa[g].m_lo) + "+" + std::to_string(fa[g].m_len) + "x" + std::to_string(fa[g].q_lo) +
+              "+" + std::to_string(fa[g].q_len);
+      auto hit = b->tuned_tt.find(tkey);
+      if (hit != b->tuned_tt.end()) {
+        b->last_tt[g] = hit->second;
+        continue;
+      }
+      int i_g = -1;
+      for (int i = 0; i < n_scans; ++i)
+        if (plan[(size_t)i].setup == (int)g && (i_g < 0 || scans[i].T > scans[i_g].T)) i_g = i;
+      float best_ms = 1e30f;
+      int best_tt = kTreeTT;
+      for (int TT : kTreeTuneTT) {
+        if (i_g < 0) break;
+        const FitArgs a = tree_args(i_g);
+        TreeRun r;
+        plan_tree(h, a, tree_lev[g], windows, n_win, dkm[g], scans[i_g].n_bl, scans[i_g].T, n_dm, a.win_off, a.S_tot,
+                  tree_budget(h), tree_tc[g] != 0 ? 0 : -1, &r, TT);
+        if (r.ser.empty()) break;
+        r.ser.resize(std::min(r.ser.size(), r.chunk));
+        if (ensure(h, h->ytree, r.need()) != cudaSuccess || tree_prepare(h) != FRBX_OK) {
+          cudaGetLastError();
+          return bfail(b, FRBX_ENOMEM, "setup " + std::to_string(g) + ": window-tree scratch");
+        }
+        FRBX_BCK(b, ensure(b->tree_ser, sizeof(int2) * r.ser.size()));
+        FRBX_BCK(b, cudaMemcpyAsync(b->tree_ser.p, r.ser.data(), sizeof(int2) * r.ser.size(), cudaMemcpyHostToDevice,
+                                    st));
+        float ms_min = 1e30f;
+        for (int rep = 0; rep < 2; ++rep) {
+          FRBX_BCK(b, cudaEventRecord(b->e0, st));
+          const int rc = enqueue_tree(h, a, r, (const int2 *)b->tree_ser.p, (char *)h->ytree.p, false, n_win, d_tab,
+                                      d_tab + woff_at[(size_t)i_g], d_tab + plan[(size_t)i_g].nval_off, st);
+          if (rc) return bfail(b, rc, "setup " + std::to_string(g) + ": " + h->err);
+          FRBX_BCK(b, cudaEventRecord(b->e1, st));
+          FRBX_BCK(b, cudaEventSynchronize(b->e1));
+          float ms = 0.f;
+          FRBX_BCK(b, cudaEventElapsedTime(&ms, b->e0, b->e1));
+          ms_min = std::min(ms_min, ms);
+        }
+        if (ms_min < best_ms) {
+          best_ms = ms_min;
+          best_tt = TT;
+        }
+      }
+      b->tuned_tt[tkey] = best_tt;
+      b->last_tt[g] = best_tt;
+    }
+    for (int i = 0; i < n_scans; ++i) {
+      const int g = plan[(size_t)i].setup;
+      if (tree_lev[(size_t)g] < 0) continue;
+      frbx_handle *h = setups[(size_t)g];
+      const FitArgs a = tree_args(i);
       targs[(size_t)i] = a;
       plan_tree(h, a, tree_lev[(size_t)g], windows, n_win, dkm[(size_t)g], scans[i].n_bl, scans[i].T, n_dm,
-                a.win_off, a.S_tot, budget, tree_tc[(size_t)g] != 0 ? 0 : -1, &truns[(size_t)i]);
+                a.win_off, a.S_tot, tree_budget(h), tree_tc[(size_t)g] != 0 ? 0 : -1, &truns[(size_t)i],
+                b->last_tt[(size_t)g]);
       need_h[(size_t)g] = std::max(need_h[(size_t)g], truns[(size_t)i].need());
       tser_off[(size_t)i] = tser_all.size();
       tser_all.insert(tser_all.end(), truns[(size_t)i].ser.begin(), truns[(size_t)i].ser.end());

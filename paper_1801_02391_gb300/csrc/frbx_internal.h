@@ -184,6 +184,11 @@ struct TreeArgs {
   int k8_steps;            // E4M3 form: K = 32 steps per AP, (2N + 31) / 32
   float *ascale;           // E4M3 form: 1 / s of every AP, [n_s][T] (s: power-of-two scale of A)
   int rot;                 // delay windows: tile row r holds SBD row (r + rot) mod Ls (multiple of 8)
+  // delay windows whose rows fit 32 or 64 tile rows: each AP keeps only its first prow rows (a
+  // piece of piece_bytes, every K atom cut to prow rows), and k_tree_mma stacks the pieces of
+  // pack = 128 / prow time tiles into one 128-row A operand (CTA: pack consecutive time tiles,
+  // n_tg groups of them per series); pack 1: whole tiles
+  int pack, prow, piece_bytes, n_tg;
   int n_abuf;              // A-tile ring depth of k_tree_mma (set by its launcher)
   int n_sanc;              // window-tree anchor levels of k_tree_mma in shared memory (set by its launcher)
 };

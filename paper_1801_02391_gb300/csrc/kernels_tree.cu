@@ -62,7 +62,8 @@ __host__ __device__ inline size_t tree_smem_bytes(int NS, int PM, int RB, int nl
 // Im Y), 128-byte swizzled K atoms: 1 = A_hi = bf16(Y) then A_lo = bf16(Y - A_hi); 2 = A_hi only;
 // 3 = E4M3 of s Y, s the power of two with s L1 <= 448 (L1 = the L1 norm of the AP's dedispersed
 // spectrum, which bounds every |Re Y|, |Im Y|), 1 / s stored in t.ascale.  Tile row r holds SBD
-// row (r + t.rot) mod Ls (rotation for delay windows; 0 for the whole grid).
+// row (r + t.rot) mod Ls (rotation for delay windows; 0 for the whole grid); with t.pack > 1
+// only the first t.prow rows of every K atom are stored (t.piece_bytes per AP).
 template <int kOut>
 __global__ void __launch_bounds__(kTreeThreads, 4)
     k_tree_sbd(const __grid_constant__ FitArgs a, const __grid_constant__ TreeArgs t) {
@@ -208,8 +209,18 @@ __global__ void __launch_bounds__(kTreeThreads, 4)
     }
     __syncthreads();
     const float4 *src = reinterpret_cast<const float4 *>(Yb);
-    float4 *dst = Yout + (size_t)k * row4;
-    for (int i = threadIdx.x; i < row4; i += blockDim.x) dst[i] = src[i];
+    if (!kOut || t.pack == 1) {
+      float4 *dst = Yout + (size_t)k * row4;
+      for (int i = threadIdx.x; i < row4; i += blockDim.x) dst[i] = src[i];
+    } else {
+      // packed delay-window form: the first prow rows of every K atom (prow * 8 float4 each)
+      float4 *dst = Yout + (size_t)k * (t.piece_bytes / 16);
+      const int per = t.prow * 8, n = (stage / tc::kAtomBytes) * per;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int c = i / per;
+        dst[i] = src[c * (tc::kAtomBytes / 16) + (i - c * per)];
+      }
+    }
     __syncthreads();
   }
 }
@@ -471,6 +482,8 @@ cudaError_t launch_tree_sbd(const FitArgs &a, const TreeArgs &t, cudaStream_t st
   const long long nb = (long long)t.n_s * t.n_ktile;
   if (nb <= 0) return cudaSuccess;
   if (!t.mma && t.rot != 0) return cudaErrorInvalidValue;
+  if (t.mma && (t.pack < 1 || t.piece_bytes * t.pack != t.tile_bytes || t.prow * t.pack != tc::kRows))
+    return cudaErrorInvalidValue;
   auto kern = !t.mma ? k_tree_sbd<0> : t.form == 0 ? k_tree_sbd<1> : t.form == 1 ? k_tree_sbd<2> : k_tree_sbd<3>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

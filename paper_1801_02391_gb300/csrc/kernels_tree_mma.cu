@@ -34,7 +34,10 @@
 // With delay search windows the SBD pass stores the rows rotated by t.rot (a multiple of 8),
 // tile row r = (m - rot) mod Ls, so the searched rows sit in the first row quarters: warps whose
 // rows are all outside the SBD window only release their slots, cells outside the windows are
-// masked, and CTAs whose 32 q lie outside the MBD window exit at once.
+// masked, and CTAs whose 32 q lie outside the MBD window exit at once.  When the searched rows
+// fit the first 32 (or 64) tile rows, the SBD pass keeps only those rows of each AP, and one CTA
+// stacks the pieces of four (or two) consecutive time tiles into its 128-row A operand: each
+// row quarter (pair) of warps walks its own time tile, so no epilogue warp idles.
 // Every wait is bounded: on timeout the kernel records FRBX_ETIMEOUT, drains and frees its
 // tensor memory.
 #include <cuda_bf16.h>
@@ -204,10 +207,15 @@ __global__ void __launch_bounds__((kEpi + 2) * 32, 1) k_tree_mma(const __grid_co
   int item = blockIdx.x;
   const int qb = item % t.n_qb;
   item /= t.n_qb;
-  const int tt = item % t.n_tt, s = item / t.n_tt;
+  const int tg = item % t.n_tg, s = item / t.n_tg;
   const int2 sd = t.series[s];
   const int kd = t.T - t.dk_max[sd.y];
-  const int kb = tt * t.TT;
+  // time tiles tg pack + p (p < pack; pack 1 outside the packed delay-window form), each with
+  // its own first AP and AP count; they only get shorter with p
+  const int pack = kFull ? 1 : t.pack, lmax = 1 << t.nlev;
+  auto tile_kb = [&](int p) { return (tg * pack + p) * t.TT; };
+  auto tile_n = [&](int p) { const int b = tile_kb(p); return b < kd ? min(kd, b + t.TT + lmax - 1) - b : 0; };
+  const int kb = tile_kb(0);
   if (kb >= kd) return;  // every segment starting here runs past the scan (uniform)
   // searched q of this block (bit j: q = 32 qb + j); none: nothing to do (uniform)
   unsigned qbmask = 0xffffffffu;
@@ -217,8 +225,7 @@ __global__ void __launch_bounds__((kEpi + 2) * 32, 1) k_tree_mma(const __grid_co
       if ((((qb * kTmNQ + j) - t.q_lo) & (t.Lm - 1)) < t.q_len) qbmask |= 1u << j;
     if (qbmask == 0u) return;
   }
-  const int ke = min(kd, kb + t.TT + (1 << t.nlev) - 1);
-  const int n_ap = ke - kb;
+  const int n_ap = tile_n(0);
   const int nbuf = t.n_abuf, n_tanc = max(t.nlev - 1, 0) - t.n_sanc;  // anchor levels in tensor memory
 
   unsigned char *sW = smem;                                   // per K atom: hi rows | lo rows
@@ -257,18 +264,34 @@ __global__ void __launch_bounds__((kEpi + 2) * 32, 1) k_tree_mma(const __grid_co
   if (warp == kLoadWarp) {
     // ================= loader: one bulk copy of the split A tiles per AP =================
     if (lane == 0) {
-      const unsigned char *src = t.Yt + (size_t)s * t.yt_series + (size_t)kb * t.tile_bytes;
+      const unsigned char *src = t.Yt + (size_t)s * t.yt_series;
       int issued = 0;
       const int n_load = t.hold ? 0 : n_ap;  // test aid: with hold, no copy is issued
+      const int n_sub = t.tile_bytes / tc::kAtomBytes, cut = t.prow * 128;
       // ring position b and the parity of its current use, advanced without a division
       for (int i = 0, b = 0, ph = 0; i < n_load; ++i) {
         if (!tc::mbar_wait(&bar_aempty[b], (uint32_t)ph ^ 1u, abortp, t.timeout)) {
           *abortp = 1;
           break;
         }
-        tc::mbar_expect_tx(&bar_afull[b], (uint32_t)t.tile_bytes);
-        tc::bulk_g2s(sA + (size_t)b * t.tile_bytes, src + (size_t)i * t.tile_bytes, (uint32_t)t.tile_bytes,
-                     &bar_afull[b]);
+        unsigned char *dst = sA + (size_t)b * t.tile_bytes;
+        if (pack == 1) {
+          tc::mbar_expect_tx(&bar_afull[b], (uint32_t)t.tile_bytes);
+          tc::bulk_g2s(dst, src + (size_t)(kb + i) * t.tile_bytes, (uint32_t)t.tile_bytes, &bar_afull[b]);
+        } else {
+          // the pieces of the tiles still running: piece p fills rows [p prow, (p + 1) prow) of
+          // every K atom; rows of finished tiles keep stale values, which only their own
+          // (idle) epilogue warps' tensor-memory lanes receive
+          int v = 1;
+          while (v < pack && i < tile_n(v)) ++v;
+          tc::mbar_expect_tx(&bar_afull[b], (uint32_t)(v * t.piece_bytes));
+          for (int p = 0; p < v; ++p) {
+            const unsigned char *ps = src + (size_t)(tile_kb(p) + i) * t.piece_bytes;
+            for (int c = 0; c < n_sub; ++c)
+              tc::bulk_g2s(dst + (size_t)c * tc::kAtomBytes + (size_t)p * cut, ps + (size_t)c * cut, (uint32_t)cut,
+                           &bar_afull[b]);
+          }
+        }
         ++issued;
         if (++b == nbuf) {
           b = 0;
@@ -362,8 +385,12 @@ __global__ void __launch_bounds__((kEpi + 2) * 32, 1) k_tree_mma(const __grid_co
     const int quarter = warp & 3, part = warp >> 2;
     const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
     const uint32_t c_re = (uint32_t)(kQ * part), c_im = (uint32_t)(kTmNQ + kQ * part);
-    // this lane's SBD row m (tile row quarter * 32 + lane, rotated by t.rot) and its first cell
-    const int m_row = (quarter * 32 + lane + t.rot) & (t.Ls - 1);
+    // this warp's time tile (its piece of the packed operand) and its first AP and AP count
+    const int qpp = 4 / pack, my_p = quarter / qpp;
+    const int kb_me = tile_kb(my_p), n_me = tile_n(my_p);
+    // this lane's SBD row m (row (quarter mod qpp) 32 + lane of its piece, rotated by t.rot) and
+    // its first cell
+    const int m_row = ((quarter % qpp) * 32 + lane + t.rot) & (t.Ls - 1);
     const unsigned idx_base = (unsigned)(m_row * t.Lm + qb * kTmNQ + kQ * part);
     // delay windows: the lane's row is searched, and which of its kQ cells
     const bool row_on = kFull || (((m_row - t.m_lo) & (t.Ls - 1)) < t.m_len);
@@ -415,7 +442,8 @@ __global__ void __launch_bounds__((kEpi + 2) * 32, 1) k_tree_mma(const __grid_co
     // non-negative floats, ordered as their bit patterns), the warp maximum, and one 64-bit
     // atomicMax into the series by the lane holding it (tied lanes share j; the atomicMax keeps
     // the lowest of their indices).
-    auto emit = [&](const int e, const int k0, const uint64_t(&gre)[kP], const uint64_t(&gim)[kP]) {
+    // i0: the segment's first AP, counted from the time tile's first AP kb_me
+    auto emit = [&](const int e, const int i0, const uint64_t(&gre)[kP], const uint64_t(&gim)[kP]) {
       float kf[kQ];
 #pragma unroll
       for (int p = 0; p < kP; ++p) {
@@ -443,14 +471,13 @@ __global__ void __launch_bounds__((kEpi + 2) * 32, 1) k_tree_mma(const __grid_co
       if (tkey == wmax && wmax != 0u) {
         const unsigned idx = idx_base + (31u - (wmax & 63u));
         // slot of the segment: windows of 2^e APs start every 2^(e-1) APs (every AP for e = 0)
-        atomicMax(keys + woff[e] + (k0 >> (e > 0 ? e - 1 : 0)),
+        atomicMax(keys + woff[e] + ((kb_me + i0) >> (e > 0 ? e - 1 : 0)),
                   ((unsigned long long)(wmax & ~63u) << 32) | (unsigned long long)(~idx));
       }
     };
     // One AP: cur receives G_1(k); prev holds G_1(k - 1).  Returns false when a wait gave up.
     auto one_ap = [&](const int i, const int slot, const uint32_t sph, const uint64_t(&pre)[kP],
                       const uint64_t(&pim)[kP], uint64_t(&cre)[kP], uint64_t(&cim)[kP]) -> bool {
-      const int k = kb + i;
       if (!__all_sync(0xffffffffu, tc::mbar_wait(&bar_accfull[slot], sph, abortp, t.timeout))) return false;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t cur = lane_base + (uint32_t)(slot * kSlotCols);
@@ -458,15 +485,16 @@ __global__ void __launch_bounds__((kEpi + 2) * 32, 1) k_tree_mma(const __grid_co
       tm_ld<kQ>(cur + c_im, cim);
 
       float inv_s = 1.f;  // E4M3 form: the AP's A was scaled by s, a power of two
-      if constexpr (kForm == kFormFp8) inv_s = __ldg(t.ascale + (size_t)s * t.T + k);
-      // levels whose window ends at k, and which of them emit a segment of this time tile
-      // (uniform across the CTA)
-      const int E = t.nlev == 0 ? 0 : min(t.nlev, __ffs(k + 1));
+      if constexpr (kForm == kFormFp8) inv_s = __ldg(t.ascale + (size_t)s * t.T + kb_me + i);
+      // levels whose window ends at AP kb_me + i, and which of them emit a segment of this time
+      // tile (uniform across the warp; kb_me is a multiple of 2^kTmMaxLev, so i's low bits
+      // decide)
+      const int E = t.nlev == 0 ? 0 : min(t.nlev, __ffs(i + 1));
       unsigned em = 0;
 #pragma unroll
       for (int e = 0; e <= kTmMaxLev; ++e) {
-        const int k0 = k - (1 << e) + 1;
-        if (e <= E && woff[e] >= 0 && k0 >= kb && k0 < kb + t.TT) em |= 1u << e;
+        const int i0 = i - (1 << e) + 1;
+        if (e <= E && woff[e] >= 0 && i0 >= 0 && i0 < t.TT) em |= 1u << e;
       }
       tm_wait_ld();
       if constexpr (kForm == kFormFp8) {
@@ -482,7 +510,7 @@ __global__ void __launch_bounds__((kEpi + 2) * 32, 1) k_tree_mma(const __grid_co
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&bar_accempty[slot]);
-      if (em & 1u) emit(0, k, cre, cim);
+      if (em & 1u) emit(0, i, cre, cim);
       if (E == 0) return true;
       uint64_t are[kP], aim[kP];
 #pragma unroll
@@ -490,7 +518,7 @@ __global__ void __launch_bounds__((kEpi + 2) * 32, 1) k_tree_mma(const __grid_co
         are[p] = add2(pre[p], cre[p]);
         aim[p] = add2(pim[p], cim[p]);
       }
-      if (em & 2u) emit(1, k - 1, are, aim);
+      if (em & 2u) emit(1, i - 1, are, aim);
 #pragma unroll
       for (int e = 2; e <= kTmMaxLev; ++e) {
         if (e > E) break;
@@ -522,20 +550,37 @@ __global__ void __launch_bounds__((kEpi + 2) * 32, 1) k_tree_mma(const __grid_co
           aim[p] = add2(aim[p], oim[p]);
         }
         if (in_tmem) tm_wait_st();
-        if ((em >> e) & 1u) emit(e, k - (1 << e) + 1, are, aim);
+        if ((em >> e) & 1u) emit(e, i - (1 << e) + 1, are, aim);
       }
       return true;
     };
     bool ok = true;
     int i = 0;
     uint32_t sph = 0;
-    for (; i + 1 < n_ap; i += 2, sph ^= 1u) {
+    for (; i + 1 < n_me; i += 2, sph ^= 1u) {
       if (!one_ap(i, 0, sph, gb_re, gb_im, ga_re, ga_im) || !one_ap(i + 1, 1, sph, ga_re, ga_im, gb_re, gb_im)) {
         ok = false;
         break;
       }
     }
-    if (ok && i < n_ap && !one_ap(i, 0, sph, gb_re, gb_im, ga_re, ga_im)) ok = false;
+    if (ok && i < n_me) {
+      if (!one_ap(i, 0, sph, gb_re, gb_im, ga_re, ga_im)) ok = false;
+      ++i;
+    }
+    // a packed time tile that ended before the CTA's first one: hand back the slots of the
+    // remaining APs (AP i uses slot i mod 2 for the (i / 2)-th time)
+    static_assert(kSlots == 2, "two accumulator slots, used alternately");
+    const int n_all = kFull ? n_me : tile_n(0);
+    for (; ok && i < n_all; ++i) {
+      const int slot = i & 1;
+      if (!__all_sync(0xffffffffu, tc::mbar_wait(&bar_accfull[slot], (uint32_t)(i >> 1) & 1u, abortp, t.timeout))) {
+        ok = false;
+        break;
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&bar_accempty[slot]);
+    }
     if (!ok) *abortp = 1;
     }
   }
@@ -572,12 +617,14 @@ cudaError_t launch_tree_mma(const TreeArgs &t, bool full, cudaStream_t st, int64
   if (t.nlev < 0 || t.nlev > kTmMaxLev || t.form < kFormSplit || t.form > kFormFp8 || t.KA != tm_katoms(t.form, t.N) ||
       t.w_bytes != tm_w_bytes(t.form, t.N) || t.tile_bytes != tm_tile_bytes(t.form, t.N) ||
       (t.form == kFormFp8 && (!t.ascale || t.k8_steps != (2 * t.N + 31) / 32)) || (full && t.rot != 0) ||
-      (t.rot & 7) != 0)
+      (t.rot & 7) != 0 || !(t.pack == 1 || t.pack == 2 || t.pack == 4) || (full && t.pack != 1) ||
+      t.prow * t.pack != tc::kRows || t.piece_bytes * t.pack != t.tile_bytes || t.n_tg * t.pack < t.n_tt ||
+      t.TT % (1 << kTmMaxLev) != 0)
     return cudaErrorInvalidValue;
   TreeArgs u = t;
   if (!tm_plan(t.form, t.N, t.nlev, &u.n_abuf, &u.n_sanc)) return cudaErrorInvalidConfiguration;
   const size_t smem = tm_smem_bytes(t.w_bytes, t.tile_bytes, u.n_abuf, u.n_sanc);
-  const long long nb = (long long)t.n_s * t.n_qb * t.n_tt;
+  const long long nb = (long long)t.n_s * t.n_qb * t.n_tg;
   if (nb <= 0) return cudaSuccess;
   if (nb > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   const unsigned g = (unsigned)nb;

@@ -168,6 +168,33 @@ def test_tree_delay_windows(frbx, kernel, sbd, mbd):
     assert am[m].all() and aq[flat["mbd_idx"].astype(int)].all()
 
 
+@pytest.mark.parametrize("sbd,pack", [((-64.0, 64.0), 4), ((-300.0, 400.0), 2), ((-600.0, 700.0), 1)])
+def test_tree_packed_delay_windows(frbx, sbd, pack):
+    """Delay windows whose searched SBD rows fit 32 (or 64) rotated tile rows: the SBD pass keeps
+    those rows of each AP and one tensor-core CTA stacks the pieces of four (or two) time tiles.
+    2600 APs make three time tiles of 1024 (the last one short and the fourth of the group
+    empty); DM 1700 sweeps past the second.  A window of 83 rows takes the whole-tile form."""
+    wl = _vgos(T=2600, n_bl=1, dms=(0.0, 1700.0))
+    wl.windows = [1, 2, 4, 8, 16, 32]
+    st = R.setup_from_workload(wl)
+    am, aq = R.window_masks(st, sbd, None)
+    m = np.flatnonzero(am)
+    lo = int(m[0]) if not (am[0] and am[-1]) else int(np.flatnonzero(am == 0)[-1]) + 1
+    nq = ((lo % 8) + int(am.sum()) + 31) // 32  # 32-row quarters holding the searched rows
+    assert {1: 4, 2: 2}.get(nq, 1) == pack
+    vis = synth.generate(wl)
+    h = frbx.Handle.from_workload(wl)
+    out = h.search(to_dev(vis), wl.dms, wl.windows, want_series=True, kernel=6, sbd_win_ns=sbd)
+    assert h.stage_times()["tree_tensor"] == 1
+    dk = R.shift_table(st, wl.dms)
+    segs, idx, _ = R.all_segments(wl.T, wl.n_bl, wl.windows, dk.max(axis=1))
+    ref = R.fit_segments(st, vis, dk, segs, am, aq)
+    flat = out["series"].reshape(-1)[idx]
+    assert (flat["amp"] >= 0).all()
+    assert_fit_match(st, vis, dk, segs, flat, ref, (am, aq))
+    assert am[flat["sbd_idx"].astype(int)].all()
+
+
 def test_tree_scan_swept_past(frbx):
     """DM trials whose sweep exceeds the scan have no valid segment; the rest are fitted."""
     wl = _vgos(T=300, n_bl=1, dms=(0.0, 2000.0))
