@@ -419,6 +419,9 @@ __global__ void __launch_bounds__((kEpi + 2) * 32, 1) k_tree_mma(const __grid_co
     int woff[kTmMaxLev + 1];  // first slot of the window emitted at each level (-1: none)
 #pragma unroll
     for (int e = 0; e <= kTmMaxLev; ++e) woff[e] = t.emit_w[e] >= 0 ? t.win_off[t.emit_w[e]] : -1;
+    unsigned wlev = 0;  // levels whose window is searched
+#pragma unroll
+    for (int e = 0; e <= kTmMaxLev; ++e) wlev |= t.emit_w[e] >= 0 ? 1u << e : 0u;
     uint64_t ga_re[kP], ga_im[kP], gb_re[kP], gb_im[kP];  // G_1 of two consecutive APs, alternating
 #pragma unroll
     for (int p = 0; p < kP; ++p) ga_re[p] = ga_im[p] = gb_re[p] = gb_im[p] = 0ull;
@@ -439,9 +442,9 @@ __global__ void __launch_bounds__((kEpi + 2) * 32, 1) k_tree_mma(const __grid_co
     tm_wait_st();
     // Maximum of one emitted segment's cells: packed keys (|G|^2 with the 6 low mantissa bits
     // replaced by 31 - j, so the lower q wins a tie), a three-input maximum tree (the keys are
-    // non-negative floats, ordered as their bit patterns), the warp maximum, and one 64-bit
-    // atomicMax into the series by the lane holding it (tied lanes share j; the atomicMax keeps
-    // the lowest of their indices).
+    // non-negative floats, ordered as their bit patterns), the warp maximum, and a 64-bit
+    // reduction-max into the series by the lane holding it, predicated rather than branched (tied
+    // lanes share j; the maximum keeps the lowest of their indices).
     // i0: the segment's first AP, counted from the time tile's first AP kb_me
     auto emit = [&](const int e, const int i0, const uint64_t(&gre)[kP], const uint64_t(&gim)[kP]) {
       float kf[kQ];
@@ -468,12 +471,14 @@ __global__ void __launch_bounds__((kEpi + 2) * 32, 1) k_tree_mma(const __grid_co
       }
       const unsigned tkey = row_on ? __float_as_uint(top) : 0u;
       const unsigned wmax = __reduce_max_sync(0xffffffffu, tkey);
-      if (tkey == wmax && wmax != 0u) {
-        const unsigned idx = idx_base + (31u - (wmax & 63u));
-        // slot of the segment: windows of 2^e APs start every 2^(e-1) APs (every AP for e = 0)
-        atomicMax(keys + woff[e] + ((kb_me + i0) >> (e > 0 ? e - 1 : 0)),
-                  ((unsigned long long)(wmax & ~63u) << 32) | (unsigned long long)(~idx));
-      }
+      // every lane forms the merge; the lanes holding the maximum issue it (predicated, no branch)
+      const unsigned idx = idx_base + (31u - (wmax & 63u));
+      // slot of the segment: windows of 2^e APs start every 2^(e-1) APs (every AP for e = 0)
+      unsigned long long *dst = keys + woff[e] + ((kb_me + i0) >> (e > 0 ? e - 1 : 0));
+      const unsigned long long kv = ((unsigned long long)(wmax & ~63u) << 32) | (unsigned long long)(~idx);
+      asm volatile("{\n .reg .pred p;\n setp.eq.u32 p, %2, %3;\n setp.ne.and.u32 p, %3, 0, p;\n"
+                   " @p red.relaxed.gpu.global.max.u64 [%0], %1;\n}\n"
+                   ::"l"(dst), "l"(kv), "r"(tkey), "r"(wmax) : "memory");
     };
     // One AP: cur receives G_1(k); prev holds G_1(k - 1).  Returns false when a wait gave up.
     auto one_ap = [&](const int i, const int slot, const uint32_t sph, const uint64_t(&pre)[kP],
@@ -490,11 +495,13 @@ __global__ void __launch_bounds__((kEpi + 2) * 32, 1) k_tree_mma(const __grid_co
       // tile (uniform across the warp; kb_me is a multiple of 2^kTmMaxLev, so i's low bits
       // decide)
       const int E = t.nlev == 0 ? 0 : min(t.nlev, __ffs(i + 1));
-      unsigned em = 0;
+      unsigned em = wlev & ((2u << E) - 1u);
+      if (i < (1 << kTmMaxLev) - 1 || i >= t.TT) {  // segments starting outside the tile (uniform, rare)
 #pragma unroll
-      for (int e = 0; e <= kTmMaxLev; ++e) {
-        const int i0 = i - (1 << e) + 1;
-        if (e <= E && woff[e] >= 0 && i0 >= 0 && i0 < t.TT) em |= 1u << e;
+        for (int e = 0; e <= kTmMaxLev; ++e) {
+          const int i0 = i - (1 << e) + 1;
+          if (i0 < 0 || i0 >= t.TT) em &= ~(1u << e);
+        }
       }
       tm_wait_ld();
       if constexpr (kForm == kFormFp8) {
