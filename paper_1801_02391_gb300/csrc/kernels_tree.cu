@@ -226,11 +226,18 @@ __global__ void __launch_bounds__(kTreeThreads, 4)
 }
 
 // ----------------------------------------------------------------------------- MBD + tree
-// Packed per-thread key: |G|^2 with its 6 low mantissa bits replaced by 32 - q2 (a 2^-17
-// relative truncation, so equal truncated powers prefer the lower q2, i.e. the lower cell).
-__device__ __forceinline__ unsigned cell_key(float2 v, int q2) {
+// Packed per-thread key of a cell, |G|^2 with its low mantissa bits replaced by a code that
+// prefers the lower q2 on equal truncated powers.  Whole grid: 4 bits, 15 - b with b = q2 div 2
+// the thread's cell rank (2^-19 relative truncation; between the two threads of a class the
+// even half h = 0 wins a tie as the lower lane), merged by one lop3 with m = ~15 kept in a
+// register.  Delay windows (fewer registers to spare): 6 bits, 32 - q2 (2^-17).
+template <bool kFull>
+__device__ __forceinline__ unsigned cell_key(float2 v, int b, int h, unsigned m) {
   const float p = fmaf(v.x, v.x, v.y * v.y);
-  return (__float_as_uint(p) & ~63u) | (unsigned)(32 - q2);
+  if constexpr (!kFull) return (__float_as_uint(p) & ~63u) | (unsigned)(32 - (2 * b + h));
+  unsigned d;
+  asm("lop3.b32 %0, %1, %2, %3, 0xE4;" : "=r"(d) : "r"(__float_as_uint(p)), "r"(15u - (unsigned)b), "r"(m));
+  return d;
 }
 
 template <int S16, bool kFull>
@@ -305,6 +312,7 @@ __global__ void __launch_bounds__(kTreeThreads, 3) k_tree_mbd(const __grid_const
   const float4 *tw4 = reinterpret_cast<const float4 *>(tw) + q1 * 2 + h;
   const int twn = PM * 2;
 
+  const unsigned kmask = 0xfffffff0u;
   // One AP: cur receives the one-AP matrix G_1(k) of the thread's cells; prev holds G_1(k - 1)
   // (the level-1 anchor).  Callers alternate the two arrays, so no anchor copy is needed.
   auto ap = [&](const int k, const float2(&prev)[16], float2(&cur)[16]) {
@@ -358,24 +366,24 @@ __global__ void __launch_bounds__(kTreeThreads, 3) k_tree_mbd(const __grid_const
         unsigned kk[16];
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
-          const unsigned kc = cell_key(acc[c], 2 * (bitrev5(c) >> 1) + h);
-          kk[c] = (cmask >> c) & 1u ? kc : 0u;
+          const unsigned kc = cell_key<kFull>(acc[c], bitrev5(c) >> 1, h, kmask);
+          kk[c] = kFull || (cmask >> c) & 1u ? kc : 0u;
         }
 #pragma unroll
         for (int wdt = 8; wdt >= 1; wdt >>= 1) {  // pairwise, so the maximum is 4 deep, not 16
 #pragma unroll
           for (int c = 0; c < wdt; ++c) kk[c] = max(kk[c], kk[c + wdt]);
         }
-        const unsigned key = kk[0];
+        const unsigned key = kFull && !row_ok ? 0u : kk[0];
         const unsigned wmax = __reduce_max_sync(0xffffffffu, key);
         const unsigned win = __ballot_sync(0xffffffffu, key == wmax);
         if (lane == 0) {
           uint2 r2 = make_uint2(0u, 0xffffffffu);
           if (wmax != 0u) {
             const int L = __ffs(win) - 1, tl = warp * 32 + L;
-            const int q2 = 32 - (int)(wmax & 63u);
+            const int q2 = kFull ? 2 * (15 - (int)(wmax & 15u)) + (half ? 0 : tl & 1) : 32 - (int)(wmax & 63u);
             const int mm = mb * RB + tl / tpr, qq1 = (tl >> 1) & (PM - 1);
-            r2 = make_uint2(wmax & ~63u, (unsigned)(mm * Lm + (half ? q2 >> 1 : qq1 + PM * q2)));
+            r2 = make_uint2(wmax & (kFull ? ~15u : ~63u), (unsigned)(mm * Lm + (half ? q2 >> 1 : qq1 + PM * q2)));
           }
           red[(buf * (kTreeMaxLev + 1) + e) * 4 + warp] = r2;
         }

@@ -156,6 +156,12 @@ __device__ __forceinline__ void tm_st(uint32_t taddr, const uint64_t (&v)[kQ / 2
                  : "memory");
   }
 }
+// (v & m) | (c & ~m) in one lop3: the high bits of v with the low bits of the immediate c
+__device__ __forceinline__ uint32_t pack_code(uint32_t v, uint32_t c, uint32_t m) {
+  uint32_t d;
+  asm("lop3.b32 %0, %1, %2, %3, 0xE4;" : "=r"(d) : "r"(v), "r"(c), "r"(m));
+  return d;
+}
 // three-input maximum of finite floats (IEEE, subnormals kept)
 __device__ __forceinline__ float fmax3(float a, float b, float c) {
   float d;
@@ -442,18 +448,19 @@ __global__ void __launch_bounds__((kEpi + 2) * 32, 1) k_tree_mma(const __grid_co
     tm_wait_st();
     // Maximum of one emitted segment's cells: packed keys (|G|^2 with the 6 low mantissa bits
     // replaced by 31 - j, so the lower q wins a tie), a three-input maximum tree (the keys are
-    // non-negative floats, ordered as their bit patterns), the warp maximum, and a 64-bit
-    // reduction-max into the series by the lane holding it, predicated rather than branched (tied
-    // lanes share j; the maximum keeps the lowest of their indices).
+    // non-negative floats, ordered as their bit patterns), the warp maximum, and one 64-bit
+    // atomicMax into the series by the lane holding it (tied lanes share j; the atomicMax keeps
+    // the lowest of their indices).
     // i0: the segment's first AP, counted from the time tile's first AP kb_me
+    const uint32_t kmask = 0xffffffc0u;  // kept in a register: one lop3 per cell packs its code
     auto emit = [&](const int e, const int i0, const uint64_t(&gre)[kP], const uint64_t(&gim)[kP]) {
       float kf[kQ];
 #pragma unroll
       for (int p = 0; p < kP; ++p) {
         uint32_t lo, hi;
         upk(fma2(gre[p], gre[p], mul2(gim[p], gim[p])), lo, hi);
-        kf[2 * p] = __uint_as_float((lo & ~63u) | (unsigned)(31 - 2 * p));
-        kf[2 * p + 1] = __uint_as_float((hi & ~63u) | (unsigned)(30 - 2 * p));
+        kf[2 * p] = __uint_as_float(pack_code(lo, 31u - 2u * p, kmask));
+        kf[2 * p + 1] = __uint_as_float(pack_code(hi, 30u - 2u * p, kmask));
       }
       if (!kFull && qmask != (1u << kQ) - 1u) {  // cells outside the MBD window (uniform per warp)
 #pragma unroll
