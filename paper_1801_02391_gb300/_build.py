@@ -56,7 +56,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         objs = list(ex.map(compile_one, SOURCES + PEAKS_SOURCES))
     for lib, part in ((LIB, objs[:len(SOURCES)]), (LIB_PEAKS, objs[len(SOURCES):])):
         tmp = lib + f".{os.getpid()}.tmp"
-        subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *part, "-lcudart"])
+        subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *part, "-lcudart", "-lpthread"])
         os.replace(tmp, lib)
     return LIB
 

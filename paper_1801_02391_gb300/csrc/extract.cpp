@@ -3,10 +3,12 @@
 // (step d), the DM merge of the coarse DM search (Sec. 5.3) and cross-matching of
 // baselines.  Sequential and O(events x window length): each insertion asks "which
 // is the first group (in creation order) holding a member whose [k0, k0 + l) overlaps
-// mine", answered from a per-AP array of the smallest group id covering that AP.
+// mine", answered from a per-AP array of the smallest group id covering that AP.  Series are
+// independent until cross-matching, so large event lists are split across host threads.
 #include <algorithm>
 #include <climits>
 #include <cmath>
+#include <thread>
 
 #include "frbx_internal.h"
 
@@ -62,10 +64,9 @@ void mbd_filter(std::vector<const frbx_event *> *grp, int Lm) {
   grp->swap(keep);
 }
 
-}  // namespace
-
-void extract_pulses(const ExtractConfig &cfg, const frbx_event *ev, int64_t n_ev, int n_series,
-                    bool use_mbd, std::vector<Pulse> *pre_merge, std::vector<Pulse> *merged) {
+// Series [s_lo, s_hi) whose events are ev[0, n_ev) (sorted by series, DM trial, window, k0).
+void extract_range(const ExtractConfig &cfg, const frbx_event *ev, int64_t n_ev, int s_lo, int s_hi,
+                   bool use_mbd, std::vector<Pulse> *pre_merge, std::vector<Pulse> *merged) {
   // window visiting order: longest first (step b)
   std::vector<int> order(cfg.n_win);
   for (int w = 0; w < cfg.n_win; ++w) order[w] = w;
@@ -75,7 +76,7 @@ void extract_pulses(const ExtractConfig &cfg, const frbx_event *ev, int64_t n_ev
   int64_t pos = 0;
   std::vector<std::vector<const frbx_event *>> groups;
   std::vector<std::pair<int64_t, int64_t>> wr(cfg.n_win);
-  for (int s = 0; s < n_series; ++s) {
+  for (int s = s_lo; s < s_hi; ++s) {
     std::vector<Pulse> series_pulses;  // DM ascending, discovery order
     for (int d = 0; d < cfg.n_dm; ++d) {
       // the events of (s, d) are contiguous and ordered by window then k0
@@ -139,6 +140,52 @@ void extract_pulses(const ExtractConfig &cfg, const frbx_event *ev, int64_t n_ev
       }
     }
     for (int i : best_of) merged->push_back(series_pulses[(size_t)i]);
+  }
+}
+
+}  // namespace
+
+// The steps above depend only on one series' own events (steps b-d per DM trial, then the DM
+// merge of that series), so contiguous runs of series go to host threads, balanced by event
+// count, and their pulses are concatenated in series order: the same output as one pass.
+void extract_pulses(const ExtractConfig &cfg, const frbx_event *ev, int64_t n_ev, int n_series,
+                    bool use_mbd, std::vector<Pulse> *pre_merge, std::vector<Pulse> *merged) {
+  const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+  int n_th = n_ev < 50000 ? 1 : std::min({n_series, hw, 32});
+  for (int64_t i = 1; i < n_ev && n_th > 1; ++i)  // split points need events sorted by series
+    if (ev[i].series < ev[i - 1].series) n_th = 1;
+  if (n_th <= 1) {
+    extract_range(cfg, ev, n_ev, 0, n_series, use_mbd, pre_merge, merged);
+    return;
+  }
+  // first event of series s (events are sorted by series)
+  auto first_of = [&](int s) -> int64_t {
+    return std::lower_bound(ev, ev + n_ev, s, [](const frbx_event &e, int v) { return e.series < v; }) - ev;
+  };
+  // series cut points: part t ends at the first series whose first event reaches (t + 1) n_ev / n_th
+  std::vector<int> cut(n_th + 1, n_series);
+  cut[0] = 0;
+  for (int t = 1; t < n_th; ++t) {
+    const int64_t target = n_ev * t / n_th;
+    int s = cut[t - 1];
+    while (s < n_series && first_of(s) < target) ++s;
+    cut[t] = s;
+  }
+  std::vector<std::vector<Pulse>> pre_part(n_th), merged_part(n_th);
+  std::vector<std::thread> th;
+  th.reserve(n_th);
+  for (int t = 0; t < n_th; ++t) {
+    if (cut[t] >= cut[t + 1]) continue;
+    th.emplace_back([&, t] {
+      const int64_t e0 = first_of(cut[t]), e1 = first_of(cut[t + 1]);
+      extract_range(cfg, ev + e0, e1 - e0, cut[t], cut[t + 1], use_mbd, pre_merge ? &pre_part[t] : nullptr,
+                    &merged_part[t]);
+    });
+  }
+  for (auto &x : th) x.join();
+  for (int t = 0; t < n_th; ++t) {
+    if (pre_merge) pre_merge->insert(pre_merge->end(), pre_part[t].begin(), pre_part[t].end());
+    merged->insert(merged->end(), merged_part[t].begin(), merged_part[t].end());
   }
 }
 

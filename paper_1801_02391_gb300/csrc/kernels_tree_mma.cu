@@ -60,6 +60,19 @@ constexpr int kTmAncBytes = tc::kRows * kTmCols * 4;  // one anchor level in sha
 // configuration of the launched instance: epilogue warps (8 or 16) and accumulator slots
 constexpr int kTmEpi = 8;
 constexpr int kTmSlots = 2;
+// Register split.  The block has three warpgroups: the eight epilogue warps (groups 0 and 1) and
+// group 2 (the MMA warp, the loader warp and two warps with no role).  Each sub-partition holds one
+// warp of every group, so at launch every thread gets 168 registers (16384 per sub-partition over
+// three warps).  Group 2 then gives registers back (setmaxnreg.dec to 56) and the epilogue groups
+// take them (setmaxnreg.inc to 224): 8 x 32 x 224 + 4 x 32 x 56 = 64512 = 384 x 168, the launch
+// allocation exactly, so the increase never waits on registers that do not exist.  The host
+// launches the kernel only when it was built with 168 registers per thread.
+constexpr int kTmWarps = kTmEpi + 4;
+constexpr int kTmLaunchRegs = 168;
+constexpr int kTmEpiRegs = 224;
+constexpr int kTmAuxRegs = 56;
+static_assert(2 * 4 * 32 * kTmEpiRegs + 4 * 32 * kTmAuxRegs == kTmWarps * 32 * kTmLaunchRegs, "register split");
+static_assert(kTmEpi == 8, "two epilogue warpgroups");
 
 // forms of the MBD product (TreeArgs::form)
 constexpr int kFormSplit = 0;  // A_hi W_hi + A_hi W_lo + A_lo W_hi in BF16 (FP32-equivalent)
@@ -194,7 +207,7 @@ __device__ __forceinline__ void mma_e4m3(uint32_t d_tmem, uint64_t ad, uint64_t 
 // anchor levels as [level][16 column quads][128 rows] float4.  kForm: the MBD product (above);
 // kFull: the whole delay grid is searched (no windows, no row rotation).
 template <int kEpi, int kSlots, int kForm, bool kFull>
-__global__ void __launch_bounds__((kEpi + 2) * 32, 1) k_tree_mma(const __grid_constant__ TreeArgs t) {
+__global__ void __launch_bounds__((kEpi + 4) * 32, 1) k_tree_mma(const __grid_constant__ TreeArgs t) {
   constexpr int kMmaWarp = kEpi, kLoadWarp = kEpi + 1;
   constexpr int kQ = kTmNQ / (kEpi / 4);   // MBD columns per epilogue thread (16 or 8)
   constexpr int kP = kQ / 2;               // packed pairs
@@ -267,6 +280,9 @@ __global__ void __launch_bounds__((kEpi + 2) * 32, 1) k_tree_mma(const __grid_co
   const uint32_t tmem = tmem_base;
   volatile int *abortp = &abort_flag;
 
+  if (warp >= kEpi) {
+  // warpgroup 2 (MMA, loader, two idle warps) hands registers to the epilogue warpgroups
+  asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kTmAuxRegs));
   if (warp == kLoadWarp) {
     // ================= loader: one bulk copy of the split A tiles per AP =================
     if (lane == 0) {
@@ -386,7 +402,9 @@ __global__ void __launch_bounds__((kEpi + 2) * 32, 1) k_tree_mma(const __grid_co
                    ::"r"(tc::su32(&bar_drain)) : "memory");
     __syncwarp();
     if (!__all_sync(0xffffffffu, tc::mbar_wait(&bar_drain, 0, nullptr, t.drain_timeout)) && leader) *abortp = 1;
+  }
   } else {
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kTmEpiRegs));
     // ================= epilogue: window tree and maxima =================
     const int quarter = warp & 3, part = warp >> 2;
     const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
@@ -453,7 +471,8 @@ __global__ void __launch_bounds__((kEpi + 2) * 32, 1) k_tree_mma(const __grid_co
     // the lowest of their indices).
     // i0: the segment's first AP, counted from the time tile's first AP kb_me
     const uint32_t kmask = 0xffffffc0u;  // kept in a register: one lop3 per cell packs its code
-    auto emit = [&](const int e, const int i0, const uint64_t(&gre)[kP], const uint64_t(&gim)[kP]) {
+    // the thread's maximum key over its kQ cells of one segment
+    auto seg_top = [&](const uint64_t(&gre)[kP], const uint64_t(&gim)[kP]) -> unsigned {
       float kf[kQ];
 #pragma unroll
       for (int p = 0; p < kP; ++p) {
@@ -476,7 +495,11 @@ __global__ void __launch_bounds__((kEpi + 2) * 32, 1) k_tree_mma(const __grid_co
         static_assert(kQ == 8, "8 or 16 cells per thread");
         top = fmax3(fmax3(kf[0], kf[1], kf[2]), fmax3(kf[3], kf[4], kf[5]), fmaxf(kf[6], kf[7]));
       }
-      const unsigned tkey = row_on ? __float_as_uint(top) : 0u;
+      return row_on ? __float_as_uint(top) : 0u;
+    };
+    // the warp maximum of a segment of level e starting at AP i0 (counted from the time tile's
+    // first AP kb_me), merged into the series by the lanes holding it when `on` (uniform)
+    auto merge = [&](const int e, const int i0, const unsigned tkey, const bool on) {
       const unsigned wmax = __reduce_max_sync(0xffffffffu, tkey);
       // every lane forms the merge; the lanes holding the maximum issue it (predicated, no branch)
       const unsigned idx = idx_base + (31u - (wmax & 63u));
@@ -484,8 +507,11 @@ __global__ void __launch_bounds__((kEpi + 2) * 32, 1) k_tree_mma(const __grid_co
       unsigned long long *dst = keys + woff[e] + ((kb_me + i0) >> (e > 0 ? e - 1 : 0));
       const unsigned long long kv = ((unsigned long long)(wmax & ~63u) << 32) | (unsigned long long)(~idx);
       asm volatile("{\n .reg .pred p;\n setp.eq.u32 p, %2, %3;\n setp.ne.and.u32 p, %3, 0, p;\n"
-                   " @p red.relaxed.gpu.global.max.u64 [%0], %1;\n}\n"
-                   ::"l"(dst), "l"(kv), "r"(tkey), "r"(wmax) : "memory");
+                   " setp.ne.and.u32 p, %4, 0, p;\n @p red.relaxed.gpu.global.max.u64 [%0], %1;\n}\n"
+                   ::"l"(dst), "l"(kv), "r"(tkey), "r"(wmax), "r"((unsigned)on) : "memory");
+    };
+    auto emit = [&](const int e, const int i0, const uint64_t(&gre)[kP], const uint64_t(&gim)[kP]) {
+      merge(e, i0, seg_top(gre, gim), true);
     };
     // One AP: cur receives G_1(k); prev holds G_1(k - 1).  Returns false when a wait gave up.
     auto one_ap = [&](const int i, const int slot, const uint32_t sph, const uint64_t(&pre)[kP],
@@ -524,15 +550,18 @@ __global__ void __launch_bounds__((kEpi + 2) * 32, 1) k_tree_mma(const __grid_co
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&bar_accempty[slot]);
-      if (em & 1u) emit(0, i, cre, cim);
-      if (E == 0) return true;
+      // levels 0 and 1 as one block without branches (their key trees interleave): G_1(k) and
+      // G_2(k - 1) = G_1(k - 1) + G_1(k), merged where their windows are emitted
       uint64_t are[kP], aim[kP];
 #pragma unroll
       for (int p = 0; p < kP; ++p) {
         are[p] = add2(pre[p], cre[p]);
         aim[p] = add2(pim[p], cim[p]);
       }
-      if (em & 2u) emit(1, i - 1, are, aim);
+      const unsigned top0 = seg_top(cre, cim), top1 = seg_top(are, aim);
+      merge(0, i, top0, (em & 1u) != 0u);
+      merge(1, i - 1, top1, (em & 2u) != 0u);
+      if (E <= 1) return true;
 #pragma unroll
       for (int e = 2; e <= kTmMaxLev; ++e) {
         if (e > E) break;
@@ -621,9 +650,14 @@ int tree_mma_w_bytes(int form, int N) { return tm_w_bytes(form, N); }
 template <int kForm, bool kFull>
 static cudaError_t launch_tm_one(const TreeArgs &u, unsigned nb, size_t smem, cudaStream_t st) {
   auto kern = k_tree_mma<kTmEpi, kTmSlots, kForm, kFull>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // the register split inside the kernel assumes the launch allocation of kTmLaunchRegs per thread
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kern);
   if (e != cudaSuccess) return e;
-  kern<<<nb, (kTmEpi + 2) * 32, smem, st>>>(u);
+  if (fa.numRegs != kTmLaunchRegs || fa.maxThreadsPerBlock < kTmWarps * 32) return cudaErrorInvalidConfiguration;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<nb, kTmWarps * 32, smem, st>>>(u);
   return cudaGetLastError();
 }
 

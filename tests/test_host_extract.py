@@ -113,3 +113,16 @@ def test_oracle_event_lists_of_the_small_workload(frbx):
     ev = to_events(rows, frbx)
     assert ev.size > 100
     compare(frbx, ev, wl.n_bl, wl.T, len(dms), wl.windows, st.Lm, 3, use_mbd=True, cross=True)
+
+
+def test_large_event_list_split_across_threads(frbx):
+    """More than 50,000 events: the library splits the series across host threads; pulses,
+    merged pulses and groups must still equal the oracle's single pass."""
+    rng = np.random.default_rng(7)
+    windows = [2, 4, 8, 16]
+    T, n_series, n_dm, Lm = 1200, 12, 3, 16
+    cands = random_events(rng, n_series, n_dm, windows, T, Lm, density=0.65)
+    ev = to_events(cands, frbx)
+    assert ev.size > 50000
+    n = compare(frbx, ev, n_series, T, n_dm, windows, Lm, 3, use_mbd=True, cross=True)
+    assert n > 0
