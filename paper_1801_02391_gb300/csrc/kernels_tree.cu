@@ -57,6 +57,13 @@ __host__ __device__ inline size_t tree_smem_bytes(int NS, int PM, int RB, int nl
 }
 
 // ----------------------------------------------------------------------------- SBD pass
+// shared -> global bulk copy (16-byte aligned addresses, a multiple of 16 bytes), completion
+// tracked by the issuing thread's bulk group
+__device__ __forceinline__ void bulk_s2g(void *dst, const void *src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(tc::su32(src)), "r"(bytes)
+               : "memory");
+}
+
 // kOut 0: FP32 rows Y[m][n] for k_tree_mbd.  kOut 1..3: each AP's output is the tensor-core A
 // operand of k_tree_mma in its shared-memory image, 128 rows x K = 2N (Re Y of the channels, then
 // Im Y), 128-byte swizzled K atoms: 1 = A_hi = bf16(Y) then A_lo = bf16(Y - A_hi); 2 = A_hi only;
@@ -131,6 +138,8 @@ __global__ void __launch_bounds__(kTreeThreads, 4)
       for (int off = 16; off; off >>= 1) l1 += __shfl_xor_sync(0xffffffffu, l1, off);
       if ((threadIdx.x & 31) == 0) red_l1[threadIdx.x >> 5] = l1;
     }
+    // the bulk copy of the previous AP's output has read the staging buffer
+    if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
     __syncthreads();
     float sc = 1.f;
     if (kOut == 3) {
@@ -207,22 +216,25 @@ __global__ void __launch_bounds__(kTreeThreads, 4)
         for (int i = 0; i < 32; ++i) Ys[(m1 + PS * bitrev5(i)) * N + n] = A[i];
       }
     }
+    // the staged output goes to device memory as bulk copies issued by one thread, which run
+    // while the next AP is gathered (the generic-proxy writes are fenced for the async proxy)
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
-    const float4 *src = reinterpret_cast<const float4 *>(Yb);
-    if (!kOut || t.pack == 1) {
-      float4 *dst = Yout + (size_t)k * row4;
-      for (int i = threadIdx.x; i < row4; i += blockDim.x) dst[i] = src[i];
-    } else {
-      // packed delay-window form: the first prow rows of every K atom (prow * 8 float4 each)
-      float4 *dst = Yout + (size_t)k * (t.piece_bytes / 16);
-      const int per = t.prow * 8, n = (stage / tc::kAtomBytes) * per;
-      for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const int c = i / per;
-        dst[i] = src[c * (tc::kAtomBytes / 16) + (i - c * per)];
+    if (threadIdx.x == 0) {
+      if (!kOut || t.pack == 1) {
+        bulk_s2g(Yout + (size_t)k * row4, Yb, (uint32_t)stage);
+      } else {
+        // packed delay-window form: the first prow rows of every K atom
+        unsigned char *dst = reinterpret_cast<unsigned char *>(Yout) + (size_t)k * t.piece_bytes;
+        const uint32_t per = (uint32_t)t.prow * 128u;
+        for (int c = 0; c < stage / tc::kAtomBytes; ++c)
+          bulk_s2g(dst + (size_t)c * per, Yb + (size_t)c * tc::kAtomBytes, per);
       }
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
     }
-    __syncthreads();
   }
+  // every copy has landed before the CTA leaves
+  if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
 // ----------------------------------------------------------------------------- MBD + tree

@@ -182,6 +182,17 @@ __device__ __forceinline__ float fmax3(float a, float b, float c) {
   return d;
 }
 __device__ __forceinline__ void tm_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// Placed after tm_wait_ld(): the values a tcgen05.ld wrote pass through this (empty, ordered)
+// statement, so no use of them can be scheduled above the wait.
+template <int kP>
+__device__ __forceinline__ void tm_hold(uint64_t (&v)[kP]) {
+  if constexpr (kP == 8) {
+    asm volatile("" : "+l"(v[0]), "+l"(v[1]), "+l"(v[2]), "+l"(v[3]), "+l"(v[4]), "+l"(v[5]), "+l"(v[6]), "+l"(v[7]));
+  } else {
+    static_assert(kP == 4, "4 or 8 packed pairs");
+    asm volatile("" : "+l"(v[0]), "+l"(v[1]), "+l"(v[2]), "+l"(v[3]));
+  }
+}
 __device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t idesc_bf16(int n) {
@@ -513,9 +524,17 @@ __global__ void __launch_bounds__((kEpi + 4) * 32, 1) k_tree_mma(const __grid_co
     auto emit = [&](const int e, const int i0, const uint64_t(&gre)[kP], const uint64_t(&gim)[kP]) {
       merge(e, i0, seg_top(gre, gim), true);
     };
-    // One AP: cur receives G_1(k); prev holds G_1(k - 1).  Returns false when a wait gave up.
-    auto one_ap = [&](const int i, const int slot, const uint32_t sph, const uint64_t(&pre)[kP],
-                      const uint64_t(&pim)[kP], uint64_t(&cre)[kP], uint64_t(&cim)[kP]) -> bool {
+    // One AP: cur receives G_1(k); pre holds G_1(k - 1).  odd: k is odd (counted from the tile's
+    // first AP, a multiple of 64), so it closes a window of 4 APs: the level-1 sum
+    // G_2(k - 1) = G_1(k - 1) + G_1(k) goes to anc_out, and G_4(k - 3) = anc_in + anc_out with
+    // anc_in = G_2(k - 3), the previous odd AP's level-1 sum (the level-2 anchor lives in
+    // registers; two arrays alternate).  deep: k + 1 is a multiple of 4, so levels 3 and up may
+    // close too (anchors in tensor memory).  odd and deep are literals at every call.  Returns
+    // false when a wait gave up.
+    auto one_ap = [&](const int i, const int slot, const uint32_t sph, const bool odd, const bool deep,
+                      const uint64_t(&pre)[kP], const uint64_t(&pim)[kP], uint64_t(&cre)[kP], uint64_t(&cim)[kP],
+                      const uint64_t(&ain_re)[kP], const uint64_t(&ain_im)[kP], uint64_t(&aout_re)[kP],
+                      uint64_t(&aout_im)[kP]) -> bool {
       if (!__all_sync(0xffffffffu, tc::mbar_wait(&bar_accfull[slot], sph, abortp, t.timeout))) return false;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t cur = lane_base + (uint32_t)(slot * kSlotCols);
@@ -537,6 +556,8 @@ __global__ void __launch_bounds__((kEpi + 4) * 32, 1) k_tree_mma(const __grid_co
         }
       }
       tm_wait_ld();
+      tm_hold<kP>(cre);
+      tm_hold<kP>(cim);
       if constexpr (kForm == kFormFp8) {
         const uint64_t iv = pk(__float_as_uint(inv_s), __float_as_uint(inv_s));
 #pragma unroll
@@ -550,20 +571,39 @@ __global__ void __launch_bounds__((kEpi + 4) * 32, 1) k_tree_mma(const __grid_co
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&bar_accempty[slot]);
-      // levels 0 and 1 as one block without branches (their key trees interleave): G_1(k) and
-      // G_2(k - 1) = G_1(k - 1) + G_1(k), merged where their windows are emitted
+      if (!odd) {
+        // levels 0 and 1 as one block without branches (their key trees interleave)
+        uint64_t are[kP], aim[kP];
+#pragma unroll
+        for (int p = 0; p < kP; ++p) {
+          are[p] = add2(pre[p], cre[p]);
+          aim[p] = add2(pim[p], cim[p]);
+        }
+        const unsigned top0 = seg_top(cre, cim), top1 = seg_top(are, aim);
+        merge(0, i, top0, (em & 1u) != 0u);
+        merge(1, i - 1, top1, (em & 2u) != 0u);
+        return true;
+      }
+      // odd AP: levels 0, 1 and 2 as one block
+#pragma unroll
+      for (int p = 0; p < kP; ++p) {
+        aout_re[p] = add2(pre[p], cre[p]);
+        aout_im[p] = add2(pim[p], cim[p]);
+      }
       uint64_t are[kP], aim[kP];
 #pragma unroll
       for (int p = 0; p < kP; ++p) {
-        are[p] = add2(pre[p], cre[p]);
-        aim[p] = add2(pim[p], cim[p]);
+        are[p] = add2(ain_re[p], aout_re[p]);
+        aim[p] = add2(ain_im[p], aout_im[p]);
       }
-      const unsigned top0 = seg_top(cre, cim), top1 = seg_top(are, aim);
+      const unsigned top0 = seg_top(cre, cim), top1 = seg_top(aout_re, aout_im), top2 = seg_top(are, aim);
       merge(0, i, top0, (em & 1u) != 0u);
       merge(1, i - 1, top1, (em & 2u) != 0u);
-      if (E <= 1) return true;
+      merge(2, i - 3, top2, ((em >> 2) & 1u) != 0u);
+      if (!deep || E <= 2) return true;
+      // levels 3 and up: anchor e - 2 of tensor memory (or shared memory) holds the first half
 #pragma unroll
-      for (int e = 2; e <= kTmMaxLev; ++e) {
+      for (int e = 3; e <= kTmMaxLev; ++e) {
         if (e > E) break;
         uint64_t ore[kP], oim[kP];
         const bool in_tmem = e - 2 < n_tanc;  // uniform
@@ -572,6 +612,8 @@ __global__ void __launch_bounds__((kEpi + 4) * 32, 1) k_tree_mma(const __grid_co
           tm_ld<kQ>(ab + c_re, ore);
           tm_ld<kQ>(ab + c_im, oim);
           tm_wait_ld();
+          tm_hold<kP>(ore);
+          tm_hold<kP>(oim);
           tm_st<kQ>(ab + c_re, are);
           tm_st<kQ>(ab + c_im, aim);
         } else {
@@ -597,21 +639,37 @@ __global__ void __launch_bounds__((kEpi + 4) * 32, 1) k_tree_mma(const __grid_co
       }
       return true;
     };
+    // AP i uses slot i mod 2 for the (i / 2)-th time, so in every group of four APs starting at
+    // a multiple of 4 the slots are 0, 1, 0, 1 and the phase parities 0, 0, 1, 1
+    uint64_t ha_re[kP], ha_im[kP], hb_re[kP], hb_im[kP];  // level-2 anchors, alternating
+#pragma unroll
+    for (int p = 0; p < kP; ++p) ha_re[p] = ha_im[p] = hb_re[p] = hb_im[p] = 0ull;
     bool ok = true;
     int i = 0;
-    uint32_t sph = 0;
-    for (; i + 1 < n_me; i += 2, sph ^= 1u) {
-      if (!one_ap(i, 0, sph, gb_re, gb_im, ga_re, ga_im) || !one_ap(i + 1, 1, sph, ga_re, ga_im, gb_re, gb_im)) {
+    for (; i + 3 < n_me; i += 4) {
+      if (!one_ap(i, 0, 0u, false, false, gb_re, gb_im, ga_re, ga_im, hb_re, hb_im, ha_re, ha_im) ||
+          !one_ap(i + 1, 1, 0u, true, false, ga_re, ga_im, gb_re, gb_im, hb_re, hb_im, ha_re, ha_im) ||
+          !one_ap(i + 2, 0, 1u, false, false, gb_re, gb_im, ga_re, ga_im, ha_re, ha_im, hb_re, hb_im) ||
+          !one_ap(i + 3, 1, 1u, true, true, ga_re, ga_im, gb_re, gb_im, ha_re, ha_im, hb_re, hb_im)) {
         ok = false;
         break;
       }
     }
+    // the last one to three APs
     if (ok && i < n_me) {
-      if (!one_ap(i, 0, sph, gb_re, gb_im, ga_re, ga_im)) ok = false;
+      ok = one_ap(i, 0, 0u, false, false, gb_re, gb_im, ga_re, ga_im, hb_re, hb_im, ha_re, ha_im);
       ++i;
+      if (ok && i < n_me) {
+        ok = one_ap(i, 1, 0u, true, false, ga_re, ga_im, gb_re, gb_im, hb_re, hb_im, ha_re, ha_im);
+        ++i;
+        if (ok && i < n_me) {
+          ok = one_ap(i, 0, 1u, false, false, gb_re, gb_im, ga_re, ga_im, ha_re, ha_im, hb_re, hb_im);
+          ++i;
+        }
+      }
     }
     // a packed time tile that ended before the CTA's first one: hand back the slots of the
-    // remaining APs (AP i uses slot i mod 2 for the (i / 2)-th time)
+    // remaining APs
     static_assert(kSlots == 2, "two accumulator slots, used alternately");
     const int n_all = kFull ? n_me : tile_n(0);
     for (; ok && i < n_all; ++i) {
