@@ -10,7 +10,7 @@
 // memory (the dropped A_lo B_lo term is below 2^-16 of each product).
 //
 // One CTA owns all Ls = 128 SBD rows of one block of 32 MBD columns q of one (baseline, DM)
-// series and walks a time tile AP by AP (10 warps):
+// series and walks a time tile AP by AP (12 warps in three warpgroups):
 //   warp 9 (one lane) copies each AP's split A tiles (written by k_tree_sbd in their
 //          shared-memory image) into a ring with cp.async.bulk;
 //   warp 8 allocates tensor memory and runs the MMA loop convergently; one elected lane issues
@@ -18,13 +18,17 @@
 //          ahead: per K step three N = 64 MMAs, A_hi W_hi, A_hi W_lo and A_lo W_hi, all
 //          accumulating into the same slot (the issue keeps pace with the tensor pipe, and the
 //          epilogue reads one 64-column result per AP);
+//   warps 10 and 11 have no role: with warps 8 and 9 they form the warpgroup that hands its
+//          registers to the epilogue (setmaxnreg), which is bound by each warp's chain of
+//          dependent work and gains from keeping more of the tree in registers;
 //   warps 0-7 (row quarter w % 4, q half w / 4) read G_1(k) into registers (freeing its slot
 //          at once), keep it there as G_1(k - 1) for the next AP, walk their 16 cells through
-//          the window tree with packed FP32x2 arithmetic (the anchors of levels 2 to 6, the
-//          first halves of windows 4 to 64, in tensor memory after the slots; shared memory
-//          takes anchor levels only where tensor memory has no room), and merge every emitted segment's
+//          the window tree with packed FP32x2 arithmetic, and merge every emitted segment's
 //          warp maximum into the series by a 64-bit atomicMax, as k_tree_mbd does per block:
-//          the warps never wait for one another.
+//          the warps never wait for one another.  The first half of a window of 4 APs (tree
+//          level 2) stays in registers; those of windows 8 to 64 (levels 3 to 6) sit in tensor
+//          memory after the slots (shared memory takes anchor levels only where tensor memory
+//          has no room).
 // Two lower-precision forms of the same tree run one product per AP instead of three: kernel 7
 // multiplies A_hi by W_hi (BF16, about 4e-3 relative on |G|), kernel 8 multiplies E4M3 operands
 // with kind::f8f6f4 (about 6e-2 relative), A scaled per AP by the power of two s with
@@ -213,9 +217,11 @@ __device__ __forceinline__ void mma_e4m3(uint32_t d_tmem, uint64_t ad, uint64_t 
 
 }  // namespace
 
-// kEpi epilogue warps, then the MMA warp and the loader warp.  Tensor memory: kSlots accumulator
-// slots of 64 columns, then the anchors of levels 2, 3, ... at 64-column steps.  Shared memory: W, the A-tile ring (t.n_abuf deep), then the t.n_sanc deepest
-// anchor levels as [level][16 column quads][128 rows] float4.  kForm: the MBD product (above);
+// kEpi epilogue warps, then the MMA warp, the loader warp and two idle warps.  Tensor memory:
+// kSlots accumulator slots of 64 columns, then one 64-column block per anchor level e >= 2 at
+// block e - 2 (level 2's block is unused: that anchor lives in registers).  Shared memory: W,
+// the A-tile ring (t.n_abuf deep), then the t.n_sanc deepest anchor levels as
+// [level][16 column quads][128 rows] float4.  kForm: the MBD product (above);
 // kFull: the whole delay grid is searched (no windows, no row rotation).
 template <int kEpi, int kSlots, int kForm, bool kFull>
 __global__ void __launch_bounds__((kEpi + 4) * 32, 1) k_tree_mma(const __grid_constant__ TreeArgs t) {
