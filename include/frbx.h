@@ -253,7 +253,10 @@ int64_t frbx_series_layout(int32_t T, const int32_t *windows, int32_t n_win, int
  *  vis      complex64 cross spectra [n_bl][T][n_chan*n_point] (interleaved re, im
  *           floats, row-major, 8-byte aligned).  If vis_on_device is nonzero it
  *           is a device pointer, else a host pointer (copied to the device inside
- *           the call; pinned memory is fastest).
+ *           the call, one baseline after another on a library stream that follows
+ *           cuda_stream, so the window-tree fit of the first baselines overlaps the
+ *           copy of the rest; pinned memory is fastest; the buffer is no longer read
+ *           once the call returns).
  *  n_bl     1..64 baselines;  T  APs (>= 1).
  *  dm       [n_dm] host, DM trials (pc cm^-3), >= 0.
  *  windows  [n_win] host, distinct window lengths in APs (>= 1), 1..16 of them.

@@ -174,13 +174,18 @@ void extract_pulses(const ExtractConfig &cfg, const frbx_event *ev, int64_t n_ev
   std::vector<std::vector<Pulse>> pre_part(n_th), merged_part(n_th);
   std::vector<std::thread> th;
   th.reserve(n_th);
+  auto part = [&](int t) {
+    const int64_t e0 = first_of(cut[t]), e1 = first_of(cut[t + 1]);
+    extract_range(cfg, ev + e0, e1 - e0, cut[t], cut[t + 1], use_mbd, pre_merge ? &pre_part[t] : nullptr,
+                  &merged_part[t]);
+  };
   for (int t = 0; t < n_th; ++t) {
     if (cut[t] >= cut[t + 1]) continue;
-    th.emplace_back([&, t] {
-      const int64_t e0 = first_of(cut[t]), e1 = first_of(cut[t + 1]);
-      extract_range(cfg, ev + e0, e1 - e0, cut[t], cut[t + 1], use_mbd, pre_merge ? &pre_part[t] : nullptr,
-                    &merged_part[t]);
-    });
+    try {
+      th.emplace_back(part, t);
+    } catch (...) {  // no thread to be had: this part runs here (no exception crosses the C ABI)
+      part(t);
+    }
   }
   for (auto &x : th) x.join();
   for (int t = 0; t < n_th; ++t) {

@@ -475,6 +475,9 @@ void frbx_destroy(frbx_handle *h) {
     if (e) cudaEventDestroy(e);
   for (cudaStream_t x : h->tree_st)
     if (x) cudaStreamDestroy(x);
+  for (cudaEvent_t e : h->vis_ev)
+    if (e) cudaEventDestroy(e);
+  if (h->copy_st) cudaStreamDestroy(h->copy_st);
   frbx_handle::Buf *bufs[] = {&h->vis, &h->dk, &h->dk_max, &h->series, &h->pnorm, &h->stats,
                               &h->counts, &h->offsets, &h->events, &h->small, &h->seglist, &h->masks,
                               &h->errflag, &h->refine, &h->calib, &h->ytree};
@@ -602,8 +605,12 @@ void fill_fit_tables(frbx_handle *h, FitArgs *a, const float2 *vis, int T, int n
   std::memcpy(a->slot_n, h->slot_n, sizeof(a->slot_n));
 }
 
+// With `copied` (host input of a search), the copy runs on the handle's copy stream one
+// baseline at a time and *copied receives the events that mark each baseline done (null for
+// device input); without it, the copy is one transfer on st.
 int check_vis(frbx_handle *h, const void *vis, int vis_on_device, int n_bl, int T, cudaStream_t st,
-              const float2 **dvis) {
+              const float2 **dvis, const cudaEvent_t **copied = nullptr) {
+  if (copied) *copied = nullptr;
   if (!vis) return fail(h, FRBX_EINVAL, "vis is NULL");
   if (n_bl < 1 || n_bl > frbx::kMaxBl) return fail(h, FRBX_EINVAL, "n_bl must be 1..64");
   if (T < 1) return fail(h, FRBX_EINVAL, "T must be >= 1");
@@ -614,8 +621,26 @@ int check_vis(frbx_handle *h, const void *vis, int vis_on_device, int n_bl, int 
     return FRBX_OK;
   }
   FRBX_CK(h, ensure(h, h->vis, bytes));
-  FRBX_CK(h, cudaMemcpyAsync(h->vis.p, vis, bytes, cudaMemcpyHostToDevice, st));
   *dvis = (const float2 *)h->vis.p;
+  if (!copied) {
+    FRBX_CK(h, cudaMemcpyAsync(h->vis.p, vis, bytes, cudaMemcpyHostToDevice, st));
+    return FRBX_OK;
+  }
+  if (!h->copy_st) FRBX_CK(h, cudaStreamCreateWithFlags(&h->copy_st, cudaStreamNonBlocking));
+  while ((int)h->vis_ev.size() < n_bl + 1) {
+    cudaEvent_t ev = nullptr;
+    FRBX_CK(h, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    h->vis_ev.push_back(ev);
+  }
+  FRBX_CK(h, cudaEventRecord(h->vis_ev[(size_t)n_bl], st));
+  FRBX_CK(h, cudaStreamWaitEvent(h->copy_st, h->vis_ev[(size_t)n_bl], 0));
+  const size_t per_bl = bytes / (size_t)n_bl;
+  for (int b = 0; b < n_bl; ++b) {
+    FRBX_CK(h, cudaMemcpyAsync((char *)h->vis.p + (size_t)b * per_bl, (const char *)vis + (size_t)b * per_bl, per_bl,
+                               cudaMemcpyHostToDevice, h->copy_st));
+    FRBX_CK(h, cudaEventRecord(h->vis_ev[(size_t)b], h->copy_st));
+  }
+  *copied = h->vis_ev.data();
   return FRBX_OK;
 }
 
@@ -805,8 +830,11 @@ void plan_tree(const frbx_handle *h, const FitArgs &a, int nlev, const int32_t *
 // passes on the other, so the SBD pass of chunk i + 1 overlaps the MBD pass of chunk i;
 // chunk parity picks the buffer set at `bufs`), then the key -> record pass.  d_ser holds
 // r.ser on the device.  With `timing`, every pass is bracketed by events for the stage times.
+// copied: per-baseline events of a cube copy still in flight (check_vis), or null; the SBD pass
+// of a chunk waits only for the baselines its series read (r.ser is baseline-major).
 int enqueue_tree(frbx_handle *h, const FitArgs &a, const TreeRun &r, const int2 *d_ser, char *bufs, bool timing,
-                 int n_win, const int *win_len, const int *win_off, const int *n_valid, cudaStream_t st) {
+                 int n_win, const int *win_len, const int *win_off, const int *n_valid, cudaStream_t st,
+                 const cudaEvent_t *copied = nullptr) {
   const frbx::TreeArgs &t = r.t;
   const size_t n_el = (size_t)r.n_bl * t.n_dm * t.S_tot;
   if (n_el == 0) return FRBX_OK;
@@ -841,6 +869,7 @@ int enqueue_tree(frbx_handle *h, const FitArgs &a, const TreeRun &r, const int2 
       cudaEvent_t *kev = timing ? h->tree_kev.data() + 4 * ci : nullptr;
       cudaError_t e = cudaSuccess;
       if (ci >= 2) e = cudaStreamWaitEvent(sA, evB[par], 0);  // the MBD pass two chunks back is done with this set
+      if (e == cudaSuccess && copied) e = cudaStreamWaitEvent(sA, copied[r.ser[c0 + (size_t)tc.n_s - 1].x], 0);
       if (e == cudaSuccess && kev) e = cudaEventRecord(kev[0], sA);
       if (e == cudaSuccess) e = frbx::launch_tree_sbd(a, tc, sA, &h->launches);
       if (e == cudaSuccess && kev) e = cudaEventRecord(kev[1], sA);
@@ -877,7 +906,8 @@ int tree_prepare(frbx_handle *h) {
 // frbx_search's window-tree fit: plan with a budget of a quarter of the free memory (at most
 // 16 GiB per buffer set), size the handle's scratch, upload the series list, enqueue.
 int run_fit_tree(frbx_handle *h, const FitArgs &a, int nlev, int form, const int32_t *windows, int n_win,
-                 const std::vector<int> &dkm, int n_bl, int T, int n_dm, const int *d_tab, int S_tot, cudaStream_t st) {
+                 const std::vector<int> &dkm, int n_bl, int T, int n_dm, const int *d_tab, int S_tot, cudaStream_t st,
+                 const cudaEvent_t *copied) {
   size_t free_b = 0, total_b = 0;
   FRBX_CK(h, cudaMemGetInfo(&free_b, &total_b));
   const size_t budget = h->lim.tree_chunk_bytes > 0 ? (size_t)h->lim.tree_chunk_bytes
@@ -897,7 +927,10 @@ int run_fit_tree(frbx_handle *h, const FitArgs &a, int nlev, int form, const int
   if (!r.ser.empty())
     FRBX_CK(h, cudaMemcpyAsync(d_ser, r.ser.data(), sizeof(int2) * r.ser.size(), cudaMemcpyHostToDevice, st));
   rc = enqueue_tree(h, a, r, d_ser, (char *)h->ytree.p + ser_bytes, true, n_win, d_tab, d_tab + frbx::kMaxWin,
-                    d_tab + 3 * frbx::kMaxWin, st);
+                    d_tab + 3 * frbx::kMaxWin, st, copied);
+  // the call's stream also follows the whole copy (series that read no baseline past some b, or
+  // none at all, leave later copies unwaited otherwise)
+  if (copied) FRBX_CK(h, cudaStreamWaitEvent(st, copied[n_bl - 1], 0));
   if (rc || !mma) return rc;
   int flag = 0;
   FRBX_CK(h, cudaMemcpyAsync(&flag, h->errflag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1121,7 +1154,8 @@ static int search_impl(frbx_handle *h, const void *vis, int32_t vis_on_device, i
   for (cudaEvent_t &ev : h->ev)
     if (!ev) FRBX_CK(h, cudaEventCreate(&ev));
   const float2 *dvis = nullptr;
-  rc = check_vis(h, vis, vis_on_device, n_bl, T, st, &dvis);
+  const cudaEvent_t *copied = nullptr;  // host input: the cube's copy runs beside the shift table
+  rc = check_vis(h, vis, vis_on_device, n_bl, T, st, &dvis, &copied);
   if (rc) return rc;
   std::vector<int> dkm;
   FRBX_CK(h, cudaEventRecord(h->ev[0], st));
@@ -1182,14 +1216,16 @@ static int search_impl(frbx_handle *h, const void *vis, int32_t vis_on_device, i
                 "2N <= 128, Lm a multiple of 32)");
   if (p.kernel == 4 || p.kernel >= 6 || (p.kernel == 0 && tree_ok)) {
     const int form = p.kernel >= 6 || (p.kernel == 0 && tree_tc) ? tc_form : -1;
-    rc = run_fit_tree(h, a, nlev, form, windows, n_win, dkm, n_bl, T, n_dm, d_tab, L.S_tot, st);
+    rc = run_fit_tree(h, a, nlev, form, windows, n_win, dkm, n_bl, T, n_dm, d_tab, L.S_tot, st, copied);
     if (rc) return rc;
   } else if (p.kernel == 3 || p.kernel == 5) {
+    if (copied) FRBX_CK(h, cudaStreamWaitEvent(st, copied[n_bl - 1], 0));
     long long nv = 0;
     for (int v : L.n_valid) nv += v;
     rc = run_fit_mma(h, a, n_bl, false, nv * n_bl, p.kernel == 5, st);
     if (rc) return rc;
   } else {
+    if (copied) FRBX_CK(h, cudaStreamWaitEvent(st, copied[n_bl - 1], 0));
     cudaError_t e = frbx::launch_fit(a, n_bl, false, p.kernel, st, &h->launches);
     if (e == cudaErrorInvalidConfiguration) return fail(h, FRBX_EUNSUPPORTED, "fit kernel does not fit this shape");
     FRBX_CK(h, e);
@@ -1206,6 +1242,7 @@ void settle(frbx_handle *h, cudaStream_t st) {
   cudaStreamSynchronize(st);
   for (cudaStream_t x : h->tree_st)
     if (x) cudaStreamSynchronize(x);
+  if (h->copy_st) cudaStreamSynchronize(h->copy_st);
   cudaGetLastError();
 }
 }  // namespace

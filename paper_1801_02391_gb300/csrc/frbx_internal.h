@@ -275,6 +275,10 @@ struct frbx_handle {
   cudaStream_t tree_st[2] = {nullptr, nullptr};  // window-tree fit: SBD passes, MBD passes
   cudaEvent_t tree_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // start, SBD done x2, MBD done x2
   std::vector<cudaEvent_t> tree_kev;  // per window-tree chunk: SBD start / end, MBD start / end
+  // host input of a search: the cube is copied one baseline after another on copy_st; vis_ev[b]
+  // marks baseline b copied, vis_ev[n_bl] the caller's stream reaching the call
+  cudaStream_t copy_st = nullptr;
+  std::vector<cudaEvent_t> vis_ev;
   int tree_chunks = 0;               // chunks of the last window-tree fit (0: another kernel ran)
   int tree_tensor = 0;               // 1: its MBD pass ran on the tensor cores (k_tree_mma)
   void *d_bimg = nullptr;  // BF16 DFT matrix image for the tensor-core fit (if supported)

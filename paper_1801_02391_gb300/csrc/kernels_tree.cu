@@ -39,7 +39,7 @@ namespace frbx {
 
 constexpr int kTreeThreads = 128;
 constexpr int kTreeMaxLev = 6;  // windows up to 64 APs
-constexpr int kSbdBatch = 8;    // SBD pass: cube loads in flight per thread
+constexpr int kSbdBatch = 16;   // SBD pass: cube loads in flight per thread
 
 // Anchors of the window tree: level 1 in registers, the next kTreeSmemAnc levels in shared
 // memory, deeper ones (touched every 16 APs or less often) in a per-CTA slice of device memory.

@@ -516,12 +516,20 @@ __global__ void __launch_bounds__((kEpi + 4) * 32, 1) k_tree_mma(const __grid_co
     };
     // the warp maximum of a segment of level e starting at AP i0 (counted from the time tile's
     // first AP kb_me), merged into the series by the lanes holding it when `on` (uniform)
+    // first slot of the tile's segments at levels 0 to 2 (kb_me is a multiple of 64, so a
+    // segment starting at tile AP i0 >= 0 sits i0 >> (e - 1) slots further; a merge of a segment
+    // starting before the tile is never issued)
+    unsigned long long *const base0 = keys + woff[0] + kb_me, *const base1 = keys + woff[1] + kb_me,
+                              *const base2 = keys + woff[2] + (kb_me >> 1);
     auto merge = [&](const int e, const int i0, const unsigned tkey, const bool on) {
       const unsigned wmax = __reduce_max_sync(0xffffffffu, tkey);
       // every lane forms the merge; the lanes holding the maximum issue it (predicated, no branch)
       const unsigned idx = idx_base + (31u - (wmax & 63u));
       // slot of the segment: windows of 2^e APs start every 2^(e-1) APs (every AP for e = 0)
-      unsigned long long *dst = keys + woff[e] + ((kb_me + i0) >> (e > 0 ? e - 1 : 0));
+      unsigned long long *dst = e == 0   ? base0 + i0
+                                : e == 1 ? base1 + i0
+                                : e == 2 ? base2 + (i0 >> 1)
+                                         : keys + woff[e] + ((kb_me + i0) >> (e - 1));
       const unsigned long long kv = ((unsigned long long)(wmax & ~63u) << 32) | (unsigned long long)(~idx);
       asm volatile("{\n .reg .pred p;\n setp.eq.u32 p, %2, %3;\n setp.ne.and.u32 p, %3, 0, p;\n"
                    " setp.ne.and.u32 p, %4, 0, p;\n @p red.relaxed.gpu.global.max.u64 [%0], %1;\n}\n"
@@ -552,8 +560,10 @@ __global__ void __launch_bounds__((kEpi + 4) * 32, 1) k_tree_mma(const __grid_co
       // levels whose window ends at AP kb_me + i, and which of them emit a segment of this time
       // tile (uniform across the warp; kb_me is a multiple of 2^kTmMaxLev, so i's low bits
       // decide)
-      const int E = t.nlev == 0 ? 0 : min(t.nlev, __ffs(i + 1));
-      unsigned em = wlev & ((2u << E) - 1u);
+      // (an even AP closes levels 0 and 1 only, an odd AP that is not deep levels 0 to 2; wlev
+      // holds no level above t.nlev)
+      const int E = !odd ? min(t.nlev, 1) : !deep ? min(t.nlev, 2) : min(t.nlev, __ffs(i + 1));
+      unsigned em = wlev & (!odd ? 3u : !deep ? 7u : (2u << E) - 1u);
       if (i < (1 << kTmMaxLev) - 1 || i >= t.TT) {  // segments starting outside the tile (uniform, rare)
 #pragma unroll
         for (int e = 0; e <= kTmMaxLev; ++e) {

@@ -79,6 +79,33 @@ def test_tree_many_chunks_matches_oracle(frbx, cut_case, kernel, series_per_chun
     assert np.array_equal(one["series"], out["series"])
 
 
+@pytest.mark.parametrize("kernel", [0, 4, 2])
+def test_host_input_copy_overlaps_the_fit(frbx, cut_case, kernel):
+    """Host input: the cube is copied one baseline after another beside the fit, and each chunk
+    of the window tree waits only for the baselines it reads.  With one series per chunk, every
+    chunk after the first runs while later baselines may still be in flight; the series, events
+    and pulses must equal those of the same search on a device copy of the cube, for the tree
+    (kernels 0, 4) and for a per-segment fit (kernel 2), which waits for the whole copy."""
+    wl, st, vis, res_o = cut_case
+    h = frbx.Handle.from_workload(wl)
+    per_series = wl.T * h.Ls * wl.n_chan * 8 + (2 << 20)
+    h.set_limits(tree_chunk_bytes=per_series)
+    dev = h.search(to_dev(vis), wl.dms, wl.windows, combos=[7], want_series=True, want_events=True,
+                   want_pre_merge=True, kernel=kernel)
+    pinned = __import__("torch").from_numpy(np.ascontiguousarray(vis)).pin_memory()
+    for host in (pinned, np.ascontiguousarray(vis)):  # pinned, then pageable host memory
+        out = h.search(host, wl.dms, wl.windows, combos=[7], want_series=True, want_events=True,
+                       want_pre_merge=True, kernel=kernel)
+        if kernel != 2:
+            assert h.stage_times()["tree_chunks"] == wl.n_bl * len(wl.dms)
+        assert np.array_equal(out["series"], dev["series"])
+        assert np.array_equal(out["events"], dev["events"])
+        assert np.array_equal(out["pulses"], dev["pulses"])
+        assert np.array_equal(out["pulses_dm"], dev["pulses_dm"])
+    if kernel == 0:  # and the oracle agrees with all of it
+        compare_search(frbx, wl, st, vis, res_o, dev, [7])
+
+
 def _sample_slots(wl, dk_max, ser, n_series, rng, tile=1024):
     """Rows (bl, d, l, k0) and series slots spread over the ordered series list (the chunk
     order), every window, the first and last valid segments and both edges of each time tile."""
