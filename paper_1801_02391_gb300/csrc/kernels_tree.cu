@@ -104,6 +104,16 @@ __global__ void __launch_bounds__(kTreeThreads, 4)
   const int dn = (int)blockDim.x / a.J, dj = (int)blockDim.x - dn * a.J;
   const int n0 = (int)threadIdx.x / a.J, j0 = (int)threadIdx.x - n0 * a.J;
   __syncthreads();
+  // When one batch covers every point, the thread's points and their offsets dk(c) C + c in the
+  // cube are fixed for the whole series: kept in registers, so no cube address waits on a
+  // shift-table load
+  const bool one_batch = a.C <= (int)blockDim.x * kSbdBatch;
+  int off[kSbdBatch];
+#pragma unroll
+  for (int q = 0; q < kSbdBatch; ++q) {
+    const int p = (int)threadIdx.x + q * (int)blockDim.x;
+    off[q] = one_batch && p < a.C ? __ldg(dk + p) * a.C + p : -1;
+  }
   for (int k = k_lo; k < k_hi; ++k) {
     // Eq. 3 with l = 1: the dedispersed spectrum of AP k, weighted and rotated; kSbdBatch
     // independent cube loads in flight per thread (the shift-table row stays in L1)
@@ -112,10 +122,16 @@ __global__ void __launch_bounds__(kTreeThreads, 4)
     float l1 = 0.f;
     for (int p0 = threadIdx.x; p0 < a.C; p0 += blockDim.x * kSbdBatch) {
       float2 v[kSbdBatch];
+      if (one_batch) {
+        const float2 *rowp = a.vis + row0 * a.C;
 #pragma unroll
-      for (int q = 0; q < kSbdBatch; ++q) {
-        const int p = p0 + q * (int)blockDim.x;
-        v[q] = p < a.C ? __ldg(a.vis + (row0 + __ldg(dk + p)) * a.C + p) : make_float2(0.f, 0.f);
+        for (int q = 0; q < kSbdBatch; ++q) v[q] = off[q] >= 0 ? __ldg(rowp + off[q]) : make_float2(0.f, 0.f);
+      } else {
+#pragma unroll
+        for (int q = 0; q < kSbdBatch; ++q) {
+          const int p = p0 + q * (int)blockDim.x;
+          v[q] = p < a.C ? __ldg(a.vis + (row0 + __ldg(dk + p)) * a.C + p) : make_float2(0.f, 0.f);
+        }
       }
 #pragma unroll
       for (int q = 0; q < kSbdBatch; ++q) {
