@@ -40,8 +40,9 @@ FIT_DRAM_BYTES_PER_SEGMENT = None
 # covers, from an ncu capture of the vgos-profile workload; None: k_tree_mbd has changed since
 # its last capture
 TREE_MBD_DRAM_BYTES_PER_AP = None
-# the same for k_tree_mma (the tensor-core MBD pass): 2.796 + 0.014 GB over 4 x 20000 series-APs
-TREE_MMA_DRAM_BYTES_PER_AP = (2.795993e9 + 0.013907e9) / (4 * 20000)
+# the same for k_tree_mma (the tensor-core MBD pass, 2048-AP time tiles): 2.701 + 0.009 GB over
+# 4 x 20000 series-APs
+TREE_MMA_DRAM_BYTES_PER_AP = (2.700700e9 + 0.009359e9) / (4 * 20000)
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 
 

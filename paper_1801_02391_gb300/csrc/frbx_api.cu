@@ -732,8 +732,8 @@ int run_stats(frbx_handle *h, StatsArgs sa, cudaStream_t st, std::vector<frbx_ev
 // builds every window from them and merges the maxima into the series buffer (as 64-bit
 // keys, zeroed first); a last pass turns the keys into frbx_seg records.  d_tab holds the
 // window tables and valid-segment counts in the layout frbx_search uploads.
-// Time tile of the window-tree fit (APs per MBD CTA, a multiple of 64); frbx_search_batch
-// measures the candidates per setup.
+// Time tile of the window-tree fit (APs per MBD CTA, a multiple of 64; frbx_search doubles it
+// for long scans on the tensor cores); frbx_search_batch measures the candidates per setup.
 constexpr int kTreeTT = 1024;
 constexpr int kTreeTuneTT[] = {512, 1024, 2048};
 
@@ -917,8 +917,11 @@ int run_fit_tree(frbx_handle *h, const FitArgs &a, int nlev, int form, const int
     FRBX_CK(h, ensure(h, h->errflag, sizeof(int)));
     FRBX_CK(h, cudaMemsetAsync(h->errflag.p, 0, sizeof(int), st));
   }
+  // long scans on the tensor cores take time tiles of 2 x kTreeTT APs: half the trailing APs
+  // each tile re-reads and half the per-CTA setup, while the grid still spans many waves
+  const int TT = mma && T >= 8 * kTreeTT ? 2 * kTreeTT : kTreeTT;
   TreeRun r;
-  plan_tree(h, a, nlev, windows, n_win, dkm, n_bl, T, n_dm, d_tab + frbx::kMaxWin, S_tot, budget, form, &r);
+  plan_tree(h, a, nlev, windows, n_win, dkm, n_bl, T, n_dm, d_tab + frbx::kMaxWin, S_tot, budget, form, &r, TT);
   int rc = tree_prepare(h);
   if (rc) return rc;
   const size_t ser_bytes = (sizeof(int2) * std::max<size_t>(r.ser.size(), 1) + 255) & ~(size_t)255;
