@@ -125,4 +125,6 @@ def test_large_event_list_split_across_threads(frbx):
     ev = to_events(cands, frbx)
     assert ev.size > 50000
     n = compare(frbx, ev, n_series, T, n_dm, windows, Lm, 3, use_mbd=True, cross=True)
+    # the combined-series form (no step c, no cross-matching) takes the same split
+    n += compare(frbx, ev, n_series, T, n_dm, windows, Lm, 3, use_mbd=False, cross=False)
     assert n > 0
